@@ -1,0 +1,48 @@
+"""The bytes-per-update model reproduces the paper's Tab. 8 from the counts
+of Tab. 1-6 (golden values as printed, tests/golden/paper_table8.txt)."""
+import os
+
+import pytest
+
+from paper_1111_0922_gb300 import model
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table8.txt")
+NAMES = {"TS": "ts", "OS": "os", "OS-NT": "os-nt", "CG": "cg", "SWAP": "swap", "AAP": "aap",
+         "ET": "et"}
+
+
+def _rows():
+    rows = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        p = line.split()
+        rows.append((p[0], int(p[1]), int(p[2]), float(p[3]), int(p[4]), int(p[5]), int(p[6]),
+                     float(p[7])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _rows(), ids=lambda r: r[0])
+def test_table8(row):
+    name, fp, fb, fc, ip, ii, ib, ic = row
+    v = NAMES[name]
+    assert model.paper_counts(v, False) == (fp, 0)
+    assert model.paper_bytes(v, False) == fb
+    assert abs(model.paper_bcode(v, False) - fc) < 0.005
+    assert model.paper_bytes(v, True) == ib
+    assert abs(model.paper_bcode(v, True) - ic) < 0.005
+    if name == "SWAP":
+        # printed counts contradict the printed bytes; Tab. 4's counts fit them
+        assert (ip, ii) == (114, 36) and ip * 8 + ii * 4 != ib
+        assert model.paper_counts(v, True) == (56, 9)
+    else:
+        assert model.paper_counts(v, True) == (ip, ii)
+
+
+def test_gpu_model_values():
+    # AA pattern / esoteric twist, indirect FP32: 2*19*4 + 9*4 = 188 bytes
+    assert model.gpu_bytes("aa", True, "f32") == 188
+    assert model.gpu_bytes("et", True, "f16s") == 112
+    assert model.gpu_bytes("os_pull", False, "f64") == 304
+    assert model.gpu_bytes("ts", True, "f64") == 4 * 19 * 8 + 18 * 4
+    assert abs(model.roof_mflups("aa", False, "f32", 6780.0) - 44605.26) < 0.1
