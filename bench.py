@@ -1,0 +1,410 @@
+"""Benchmark of the D3Q19 step on GB300.
+
+Headline workload: a periodic 256^3 full grid (direct addressing), density
+rho = 1 + 1e-3 U[-1, 1) (SplitMix64 seed 2), zero velocity, omega = 1.7,
+AA pattern, FP32 storage of f - w, SoA.  One bench step is one time step of
+the whole lattice (one kernel launch for the AA pattern).  The state (1.27 GB)
+is larger than L2 (129 MB), so no flush is needed between steps.
+
+Printed (rank 0, one JSON line): MFLUP/s of the headline run, the roofline of
+its kernel against the measured HBM copy bandwidth, an end-to-end figure
+through the C ABI with host buffers, the FP64 CPU oracle timed on the host
+cores, SM clocks sampled during the timed region, and a sweep over every
+propagation scheme x FP64/FP32 x SoA/AoS with each one's fraction of its own
+roofline.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gb300|reference]
+N > 1 runs under torchrun as N independent replicas (weak scaling, no
+collective on the data path); value = total node updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1111_0922_gb300 import inputs, model  # noqa: E402
+
+METRIC = "D3Q19 MFLUP/s & % of HBM roofline per propagation variant; solves/s, p99"
+DIMS = (256, 256, 256)
+OMEGA = 1.7
+SEED = 2
+WORKLOAD = "periodic 256^3 full grid, rho = 1 + 1e-3 U[-1,1) (seed 2), u = 0, omega = 1.7, BGK"
+FALLBACK_HBM = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM)), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1111_0922_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the kernel sources changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = np.array([float(r[1]) for r in rows])
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = sm[sm > 0.5 * mx] if np.any(sm > 0.5 * mx) else sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": int(sm.size), "power_w_max": max(float(r[3]) for r in rows
+                                                             if r[3].replace(".", "").isdigit())}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # noqa: BLE001
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+# ---------------------------------------------------------------------------
+def make_lattice(lbm, variant, precision, layout, addressing="direct", dims=DIMS, omega=OMEGA,
+                 force=(0.0, 0.0, 0.0), **kw):
+    return lbm.Lattice(dims, (1, 1, 1), variant=variant, addressing=addressing, layout=layout,
+                       precision=precision, omega=omega, force=force, **kw)
+
+
+def timed_steps(torch, lat, steps, per_launch=True):
+    """Run `steps` steps between CUDA events on the lattice's stream.
+    Returns (total seconds, mean seconds per launch-step)."""
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1 if per_launch else 2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for t in range(steps):
+        lat.step(1)
+        if per_launch:
+            ev[t + 1].record(stream)
+    if not per_launch:
+        ev[1].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[-1]) / 1e3
+    if per_launch:
+        durs = [ev[t].elapsed_time(ev[t + 1]) / 1e3 for t in range(steps)]
+        return total, float(np.mean(durs))
+    return total, total / steps
+
+
+def run_headline(torch, lbm, args, rank, world):
+    dev = torch.cuda.current_device()
+    n = int(np.prod(DIMS))
+    rho_host = inputs.density_noise(DIMS, seed=SEED)
+    rho_dev = torch.from_numpy(rho_host).to(f"cuda:{dev}")
+    lat = make_lattice(lbm, "aa", "f32", "soa")
+    lat.set_geometry(None)
+    lat.init(rho_dev, on_device=True)
+    lat.step(args.warmup if args.warmup % 2 == 0 else args.warmup + 1)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_smi_id(torch, dev))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total, per_launch = timed_steps(torch, lat, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    info = lat.info
+    t_max = total
+    if world > 1:
+        t = torch.tensor([total], device=f"cuda:{dev}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    kernels = args.steps * info.kernels_per_step
+    lat.close()
+    del rho_dev
+    return {"total_s": t_max, "per_launch_s": per_launch, "nodes": n, "clocks": clocks,
+            "kernels": kernels, "rho_host": rho_host}
+
+
+def run_e2e(torch, lbm, args, rho_host):
+    """The same solve through the public API with host buffers: the initial
+    density goes up from pinned host memory, the mass/flux come back every 100
+    steps through the fused reduction, and the final density field comes back
+    to pinned host memory, all inside the timed region."""
+    n = rho_host.size
+    pin_rho = torch.from_numpy(rho_host).pin_memory()
+    pin_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    lat = make_lattice(lbm, "aa", "f32", "soa")
+    lat.set_geometry(None)
+    check = 100
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.init(pin_rho.numpy())
+    done = 0
+    reads = 0
+    while done < args.steps:
+        k = min(check, args.steps - done)
+        if k % 2 == 1 and k > 1:
+            k -= 1
+        lat.step_flux(k)
+        reads += 1
+        done += k
+    if done % 2 == 1:  # AA pattern reads out after an even count
+        lat.step(1)
+        done += 1
+    lbm.lbm_macroscopics(lat.h, n, rho=pin_out.numpy(), want_u=False)
+    t1 = time.perf_counter()
+    lat.close()
+    secs = t1 - t0
+    return {"value": n * done / secs / 1e6, "unit": "MFLUP/s",
+            "h2d_bytes_per_step": int(8 * n / done), "d2h_bytes_per_step": int((8 * n + 16 * reads) / done),
+            "seconds": secs}
+
+
+def run_cpu_baseline(target_s=10.0):
+    """The FP64 oracle as it stands (push definition, OpenMP over cells) on
+    the host cores: 256^3 periodic from the same initial state, whole steps
+    until about target_s seconds have passed."""
+    import oracle
+
+    oracle.build()
+    threads = oracle.default_threads()
+    rho = inputs.density_noise(DIMS, seed=SEED)
+    _, w = oracle.lattice()
+    f = np.ascontiguousarray(w[:, None] * rho[None, :])
+    n = rho.size
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < target_s:
+        f = oracle.push_full(DIMS, (1, 1, 1), None, f, OMEGA, nthreads=threads)
+        steps += 1
+    secs = time.perf_counter() - t0
+    return {"value": n * steps / secs / 1e6, "unit": "MFLUP/s", "cores": threads, "kind": "oracle",
+            "sample": "%d full steps of the 256^3 periodic box (%.1f s)" % (steps, secs)}
+
+
+def run_sweep(torch, lbm, args, hbm):
+    """Every scheme x FP64/FP32 x SoA/AoS on the headline workload."""
+    out = {}
+    n = int(np.prod(DIMS))
+    rho_dev = torch.from_numpy(inputs.density_noise(DIMS, seed=SEED)).cuda()
+    for variant in model.VARIANTS:
+        for precision in ("f64", "f32"):
+            for layout in ("soa", "aos"):
+                key = "%s/%s/%s" % (variant, precision, layout)
+                try:
+                    lat = make_lattice(lbm, variant, precision, layout)
+                    lat.set_geometry(None)
+                    lat.init(rho_dev, on_device=True)
+                    lat.step(4)
+                    steps = args.sweep_steps
+                    total, per = timed_steps(torch, lat, steps, per_launch=False)
+                    mflups = n * steps / total / 1e6
+                    roof = model.roof_mflups(variant, False, precision, hbm)
+                    out[key] = {"mflups": round(mflups, 1), "roof_mflups": round(roof, 1),
+                                "frac": round(mflups / roof, 4),
+                                "bytes_per_flup": model.gpu_bytes(variant, False, precision),
+                                "kernels_per_step": lat.info.kernels_per_step}
+                    lat.close()
+                except lbm.LBMError as e:
+                    out[key] = {"unsupported": str(e).split(": ", 1)[-1][:120]}
+                torch.cuda.empty_cache()
+                log("sweep", key, out[key])
+    del rho_dev
+    torch.cuda.empty_cache()
+    return out
+
+
+def main_gb300(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1111_0922_gb300 import build, lbm
+
+    build.build()
+    lbm.load()
+    hbm, peak_kind = measured_peaks()
+    head = run_headline(torch, lbm, args, rank, world)
+    n = head["nodes"]
+    value = world * n * args.steps / head["total_s"] / 1e6
+    bytes_launch = n * model.kernel_bytes_per_flup("aa", False, "f32")
+    achieved = bytes_launch / head["per_launch_s"] / 1e9
+    traffic = profiled_traffic("aa_f32_soa_direct_256")
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MFLUP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["total_s"] / args.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": "aa", "precision": "f32 (f - w stored)",
+                   "layout": "soa", "addressing": "direct", "nodes_per_gpu": n,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "state 1.27 GB > 129 MB L2, no flush needed"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                     "bytes_per_launch": int(bytes_launch), "traffic": traffic,
+                     "kernel": "k_aa_even/k_aa_odd<CodecF32,SoA,direct>"},
+        "gpu_launches": head["kernels"],
+        "clocks": head["clocks"],
+    }
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = run_e2e(torch, lbm, args, head["rho_host"])
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = run_cpu_baseline(args.cpu_seconds)
+    if rank == 0 and not args.no_sweep:
+        result["variants"] = run_sweep(torch, lbm, args, hbm)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main_reference(args):
+    """The FP64 CPU oracle on the host cores, same workload and metric; each
+    step is one oracle step over a bounded sample: a 256 x 256 x 16 periodic
+    slab cut from the same initial state."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    threads = oracle.default_threads()
+    dims = (256, 256, 16)
+    rho = inputs.density_noise(DIMS, seed=SEED)[: int(np.prod(dims))]
+    _, w = oracle.lattice()
+    f = np.ascontiguousarray(w[:, None] * rho[None, :])
+    for _ in range(args.warmup):
+        f = oracle.push_full(dims, (1, 1, 1), None, f, OMEGA, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.push_full(dims, (1, 1, 1), None, f, OMEGA, nthreads=threads)
+    secs = time.perf_counter() - t0
+    n = int(np.prod(dims))
+    value = n * args.steps / secs / 1e6
+    sample = "each step: one oracle step of a 256x256x16 periodic slab (%d nodes) of the workload" % n
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MFLUP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": "push definition (oracle)", "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MFLUP/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MFLUP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--sweep-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    a = ap.parse_args(argv)
+    if a.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if a.steps < 1:
+        ap.error("--steps must be >= 1")
+    return a
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_gb300(args)

@@ -1,0 +1,193 @@
+/*
+ * liblbm — GB300 (sm_103a) D3Q19 lattice Boltzmann time step, C ABI.
+ *
+ * One time step is the BGK collision (with a constant body force, Guo's
+ * forcing term) at every fluid node followed by the propagation of the
+ * post-collision PDFs to the neighbours, with half-way bounce-back at solid
+ * nodes and at non-periodic box faces.  The propagation is done by one of the
+ * schemes compared by Wittmann, Zeiser, Hager and Wellein, "Comparison of
+ * different Propagation Steps for the Lattice Boltzmann Method":
+ *
+ *   LBM_TS       two-step: collide kernel + separate stream kernel  (Sec. 2, Tab. 1)
+ *   LBM_OS_PUSH  one-step push, two lattices                         (Sec. 3, Fig. 1a,b, Tab. 2)
+ *   LBM_OS_PULL  one-step pull, two lattices                         (Sec. 3, Fig. 1c,d)
+ *   LBM_CG       compressed grid, one lattice shifted between steps  (Sec. 4, Fig. 2, Tab. 3)
+ *   LBM_SWAP     swap, one lattice, link exchanges                   (Sec. 5, Fig. 3, Tab. 4)
+ *   LBM_AA       AA pattern, one lattice, even/odd kernels           (Sec. 6, Fig. 5, Tab. 5)
+ *   LBM_ET       esoteric twist, one lattice, array pointer swap     (Sec. 7, Fig. 6, Tab. 6)
+ *
+ * on a full grid (LBM_DIRECT: neighbours by index arithmetic) or on a list of
+ * fluid nodes with an int32 adjacency array IDX (LBM_INDIRECT), with the PDFs
+ * in structure-of-arrays (LBM_SOA, one array per direction) or
+ * array-of-structures (LBM_AOS) layout (Sec. 1).
+ *
+ * Precision: LBM_F64 stores f_i - w_i in FP64 and computes in FP64;
+ * LBM_F32 stores f_i - w_i in FP32 and computes in FP32; LBM_F16S stores
+ * round((f_i - w_i) * S) in FP16 with a power-of-two scale S and computes in
+ * FP32.  Mass and flux sums are always accumulated in FP64.
+ *
+ * Conventions
+ *   velocities  0:(0,0,0) 1:(+1,0,0) 2:(-1,0,0) 3:(0,+1,0) 4:(0,-1,0)
+ *               5:(0,0,+1) 6:(0,0,-1) 7:(+1,+1,0) 8:(-1,-1,0) 9:(+1,-1,0)
+ *               10:(-1,+1,0) 11:(+1,0,+1) 12:(-1,0,-1) 13:(+1,0,-1)
+ *               14:(-1,0,+1) 15:(0,+1,+1) 16:(0,-1,-1) 17:(0,+1,-1)
+ *               18:(0,-1,+1); weights 1/3, 1/18 (1-6), 1/36 (7-18).
+ *   cells       x fastest: cell = x + nx * (y + ny * z).
+ *   nodes       fluid cells numbered in that order (lexicographic).
+ *   natural     the pre-collision state f_i(x) after a whole number of
+ *               steps, as a host or device array f[i * n + k] (FP64), k the
+ *               cell (direct) or node (indirect).
+ *   velocity    u = (sum_i c_i f_i + rho g / 2) / rho.
+ *
+ * Ownership: the library owns every device buffer it allocates; it allocates
+ * through cfg->dev_alloc / cfg->dev_free when given (e.g. PyTorch's caching
+ * allocator), else cudaMalloc / cudaFree, and only inside lbm_create,
+ * lbm_set_geometry* and lbm_destroy.  Host pointers are borrowed for the call.
+ * Device pointers passed with on_device = 1 must be on the handle's device.
+ *
+ * Errors: every call returns a status and never throws.  lbm_last_error
+ * gives a one-line reason.  Kernels are enqueued on cfg->stream and run
+ * asynchronously; launch errors are reported by the call, device-side errors
+ * (bounds flags of a checked build) by the next synchronising call.
+ * A handle must not be used from two threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = 1,  /* bad pointer, size, enum or configuration */
+  LBM_ERR_OOM = 2,          /* a device allocation failed */
+  LBM_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed */
+  LBM_ERR_STATE = 4,        /* call not valid in the handle's current state */
+  LBM_ERR_BOUNDS = 5,       /* a kernel's bounds check tripped */
+  LBM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+  LBM_ERR_NOT_CONVERGED = 7,/* a solve hit its step cap */
+  LBM_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
+} lbm_status;
+
+enum { LBM_TS = 0, LBM_OS_PUSH = 1, LBM_OS_PULL = 2, LBM_CG = 3, LBM_SWAP = 4, LBM_AA = 5, LBM_ET = 6 };
+enum { LBM_DIRECT = 0, LBM_INDIRECT = 1 };
+enum { LBM_SOA = 0, LBM_AOS = 1 };
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 };
+
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, size_t bytes, void *ctx);
+
+typedef struct lbm_config {
+  int32_t nx, ny, nz;        /* bounding box, each >= 1; periodic extents >= 2 */
+  int32_t periodic[3];       /* 1 = periodic axis, 0 = bounce-back walls beyond both faces */
+  int32_t variant;           /* LBM_TS .. LBM_ET */
+  int32_t addressing;        /* LBM_DIRECT or LBM_INDIRECT */
+  int32_t layout;            /* LBM_SOA or LBM_AOS */
+  int32_t precision;         /* LBM_F64, LBM_F32, LBM_F16S */
+  double omega;              /* BGK relaxation rate, 0 < omega < 2 (0 = identity collision) */
+  double force[3];           /* body acceleration g (Guo forcing) */
+  double f16_scale;          /* LBM_F16S: scale S (power of two); 0 = choose from force */
+  int32_t block_size;        /* threads per block (multiple of 32, <= 1024); 0 = default 256 */
+  int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default */
+  int32_t cg_shift;          /* LBM_CG: shift k in planes (direct) >= 2; 0 = default */
+  int32_t reserved;
+  void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
+  lbm_alloc_fn dev_alloc;    /* optional device allocator */
+  lbm_free_fn dev_free;      /* required when dev_alloc is given */
+  void *alloc_ctx;           /* passed to dev_alloc / dev_free */
+} lbm_config;
+
+typedef struct lbm_info {
+  int64_t cells;             /* nx * ny * nz */
+  int64_t nodes;             /* fluid nodes (direct: cells; the solid ones are skipped) */
+  int64_t storage_nodes;     /* slots per PDF array incl. ghosts, halos, shifts, padding */
+  int64_t state_bytes;       /* device bytes of PDF storage */
+  int64_t index_bytes;       /* device bytes of IDX and other per-node index data */
+  int64_t steps;             /* time steps done since lbm_init / lbm_set_pdfs */
+  int32_t natural;           /* 1 if the state can be read out (AA: even step count) */
+  int32_t kernels_per_step;  /* launches one lbm_step(h, 1) makes */
+  double f16_scale;          /* scale in use (LBM_F16S) */
+  int32_t reduce_blocks;     /* blocks of the fused reduction */
+  int32_t reserved;
+} lbm_info;
+
+typedef struct lbm lbm_t;
+
+/* Fill *cfg with defaults: 32^3 periodic box, LBM_AA, direct, SoA, FP32,
+ * omega 1, no force, default launch shape, default stream, cudaMalloc. */
+lbm_status lbm_config_default(lbm_config *cfg);
+
+/* Validate cfg and create a handle on the current CUDA device.  No geometry
+ * yet: call lbm_set_geometry or lbm_set_geometry_spheres next. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_t **out);
+
+/* Free every device buffer (waits for the handle's stream).  NULL is OK. */
+lbm_status lbm_destroy(lbm_t *h);
+
+/* One-line description of the last failure on h (or a global one if h is NULL). */
+const char *lbm_last_error(const lbm_t *h);
+const char *lbm_status_string(lbm_status s);
+
+/* Geometry (Sec. 1; the packed bed of Fig. 7, Sec. 10).  solid_mask_host:
+ * nx*ny*nz bytes, x fastest, nonzero = solid, or NULL for an all-fluid box.
+ * Builds on the GPU the fluid-node list (lexicographic) and, for
+ * LBM_INDIRECT, IDX[18][N] (IDX[i-1][k] = node reached from node k along
+ * c_i, -1 for a solid or wall link) plus the variant's own index data;
+ * allocates the PDF storage.  Resets the state to rest (f = w). Synchronises. */
+lbm_status lbm_set_geometry(lbm_t *h, const uint8_t *solid_mask_host);
+
+/* Same, with the solid mask generated on the GPU from overlapping spheres:
+ * a cell is solid iff the minimum-image distance (periodic axes) between its
+ * centre and some sphere centre is <= radius.  centres_host: nsph x 3 int64
+ * positions and the radius in units of 1/unit cells (exact integer test). */
+lbm_status lbm_set_geometry_spheres(lbm_t *h, int64_t nsph, const int64_t *centres_host,
+                                    int64_t radius, int64_t unit);
+
+/* Read back geometry: the solid mask (nx*ny*nz bytes), the node list
+ * (node -> cell, N int32) and IDX (18*N int32, direction-major).  Host
+ * buffers.  lbm_get_idx is valid for LBM_INDIRECT only.  Synchronise. */
+lbm_status lbm_get_mask(lbm_t *h, uint8_t *mask_host);
+lbm_status lbm_get_nodes(lbm_t *h, int32_t *cells_host);
+lbm_status lbm_get_idx(lbm_t *h, int32_t *idx_host);
+lbm_status lbm_get_info(const lbm_t *h, lbm_info *info);
+
+/* Initial state f_i = f_eq(rho, u) per node (direct: per cell, solid cells
+ * ignored).  rho: n doubles or NULL (= 1); u: 3n doubles (x,y,z per node) or
+ * NULL (= 0).  on_device = 1: the pointers are device memory.  Pull-type
+ * schemes store the pre-image of this state under streaming.  Step count 0. */
+lbm_status lbm_init(lbm_t *h, const double *rho, const double *u, int on_device);
+
+/* Set / get the natural state f[i * n + k] (FP64, n = nodes or cells).
+ * get requires a natural state (LBM_AA: even step count) else LBM_ERR_STATE;
+ * solid cells of a direct grid read back as 0.  get synchronises. */
+lbm_status lbm_set_pdfs(lbm_t *h, const double *f, int on_device);
+lbm_status lbm_get_pdfs(lbm_t *h, double *f, int on_device);
+
+/* Enqueue n >= 0 time steps on cfg->stream; returns without waiting. */
+lbm_status lbm_step(lbm_t *h, int n);
+
+/* Enqueue n >= 1 steps; the first kernel also reduces, in FP64 with a fixed
+ * summation order, the mass sum(rho) and the flux sum(rho u_x) of the state
+ * the call starts from, over all fluid nodes.  Requires a natural starting
+ * state.  mass / jx are host pointers; the call synchronises. */
+lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx);
+
+/* Mass and flux of the current (natural) state, FP64, fixed order.  Syncs. */
+lbm_status lbm_flux(lbm_t *h, double *mass, double *jx);
+
+/* Density (n) and velocity (3n) of the current natural state; either
+ * pointer may be NULL.  Synchronises when on_device = 0. */
+lbm_status lbm_macroscopics(lbm_t *h, double *rho, double *u, int on_device);
+
+/* Wait for the handle's stream and report device-side errors. */
+lbm_status lbm_sync(lbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,822 @@
+// C ABI of liblbm (declared in include/lbm.h): handle life cycle, geometry
+// set-up, state in/out, time stepping and reductions.  Host code only; every
+// step of the path runs in the kernels of lbm_steps.cu, lbm_cg.cu,
+// lbm_swap.cu and lbm_setup.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmk;
+
+struct lbm {
+  lbm_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<std::pair<void *, size_t>> geo_allocs;  // freed on re-geometry / destroy
+  std::vector<std::pair<void *, size_t>> base_allocs; // freed on destroy
+  bool has_geometry = false;
+  int64_t cells = 0, nodes = 0, nghost = 0;
+  int64_t nn = 0;    // node space of a launch (direct: cells, indirect: fluid nodes)
+  int64_t slots = 0; // storage slots per PDF array
+  int64_t npad = 0;  // SoA stride
+  int64_t ipad = 0;
+  uint8_t *d_solid = nullptr;
+  bool any_solid = false;
+  int32_t *d_cells = nullptr, *d_idx = nullptr, *d_etidx = nullptr;
+  void *d_A = nullptr, *d_B = nullptr;
+  size_t state_bytes = 0;
+  int64_t index_bytes = 0;
+  double *d_partials = nullptr;
+  int partial_blocks = 0;
+  double *d_out2 = nullptr;
+  double *h_out2 = nullptr;  // pinned
+  int *d_err = nullptr;
+  Grid grid{};
+  int map[Q];
+  int64_t steps = 0;
+  float scale = 1.0f;
+  int cg_k = 0, cg_o = 0;
+  int swap_tile[3] = {0, 0, 0};
+};
+
+static std::string g_last_error;
+
+static lbm_status fail(lbm_t *h, lbm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(h, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(h, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static lbm_status check_launch(lbm_t *h, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+static void *dalloc(lbm_t *h, size_t bytes, std::vector<std::pair<void *, size_t>> &list) {
+  if (bytes == 0) bytes = 256;
+  void *p = nullptr;
+  if (h->cfg.dev_alloc) {
+    p = h->cfg.dev_alloc(bytes, h->cfg.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) list.emplace_back(p, bytes);
+  return p;
+}
+
+static void dfree(lbm_t *h, void *p, size_t bytes) {
+  if (!p) return;
+  if (h->cfg.dev_free)
+    h->cfg.dev_free(p, bytes, h->cfg.alloc_ctx);
+  else
+    cudaFree(p);
+}
+
+static void free_list(lbm_t *h, std::vector<std::pair<void *, size_t>> &list) {
+  for (auto &a : list) dfree(h, a.first, a.second);
+  list.clear();
+}
+
+// temporary device buffer freed at scope exit (after a stream sync)
+struct TempBuf {
+  lbm_t *h;
+  void *p = nullptr;
+  size_t n = 0;
+  TempBuf(lbm_t *h_, size_t bytes) : h(h_), n(bytes) {
+    std::vector<std::pair<void *, size_t>> l;
+    p = dalloc(h, bytes, l);
+  }
+  ~TempBuf() {
+    if (p) {
+      cudaStreamSynchronize(h->stream);
+      dfree(h, p, n);
+    }
+  }
+};
+
+static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+static size_t store_size(int precision) { return precision == LBM_F64 ? 8 : (precision == LBM_F32 ? 4 : 2); }
+
+static bool two_lattices(int variant) {
+  return variant == LBM_TS || variant == LBM_OS_PUSH || variant == LBM_OS_PULL;
+}
+
+static int map_kind(const lbm_t *h) {
+  switch (h->cfg.variant) {
+    case LBM_OS_PULL:
+    case LBM_CG:
+      return MAP_PULL;
+    case LBM_ET:
+      return MAP_ET;
+    default:
+      return MAP_NATURAL;
+  }
+}
+
+static bool is_natural(const lbm_t *h) { return h->cfg.variant != LBM_AA || (h->steps & 1) == 0; }
+
+static KernelKey key_of(const lbm_t *h, bool red) {
+  KernelKey k;
+  k.precision = h->cfg.precision;
+  k.aos = h->cfg.layout == LBM_AOS;
+  k.ind = h->cfg.addressing == LBM_INDIRECT;
+  k.force = h->cfg.force[0] != 0.0 || h->cfg.force[1] != 0.0 || h->cfg.force[2] != 0.0;
+  k.red = red;
+  return k;
+}
+
+static StepParams params_of(const lbm_t *h) {
+  StepParams p;
+  memset(&p, 0, sizeof p);
+  p.A = h->d_A;
+  p.B = h->d_B;
+  p.npad = h->npad;
+  p.nnodes = h->nn;
+  p.nfluid = h->nodes;
+  p.g = h->grid;
+  p.idx = h->cfg.variant == LBM_ET ? h->d_etidx : h->d_idx;
+  p.ipad = h->ipad;
+  for (int i = 0; i < Q; ++i) p.map[i] = h->map[i];
+  p.omega = h->cfg.omega;
+  p.gx = h->cfg.force[0];
+  p.gy = h->cfg.force[1];
+  p.gz = h->cfg.force[2];
+  p.scale = h->scale;
+  p.inv_scale = 1.0f / h->scale;
+  p.partials = h->d_partials;
+  p.err = h->d_err;
+  return p;
+}
+
+static LaunchShape shape_of(const lbm_t *h) {
+  LaunchShape L;
+  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 256;
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
+  int64_t blocks = (h->nn + (int64_t)bs * npt - 1) / ((int64_t)bs * npt);
+  if (blocks < 1) blocks = 1;
+  L.grid = dim3((unsigned)blocks);
+  L.block = dim3((unsigned)bs);
+  L.stream = h->stream;
+  return L;
+}
+
+static StateDesc state_desc(const lbm_t *h) {
+  StateDesc d;
+  d.p = params_of(h);
+  d.k = key_of(h, false);
+  d.mapkind = map_kind(h);
+  d.cells = h->d_cells;
+  return d;
+}
+
+extern "C" {
+
+const char *lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_STATE: return "invalid state";
+    case LBM_ERR_BOUNDS: return "bounds check failed";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_NOT_CONVERGED: return "not converged";
+    case LBM_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *lbm_last_error(const lbm_t *h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+lbm_status lbm_config_default(lbm_config *cfg) {
+  if (!cfg) return fail(nullptr, LBM_ERR_INVALID_ARG, "cfg is NULL");
+  memset(cfg, 0, sizeof *cfg);
+  cfg->nx = cfg->ny = cfg->nz = 32;
+  cfg->periodic[0] = cfg->periodic[1] = cfg->periodic[2] = 1;
+  cfg->variant = LBM_AA;
+  cfg->addressing = LBM_DIRECT;
+  cfg->layout = LBM_SOA;
+  cfg->precision = LBM_F32;
+  cfg->omega = 1.0;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
+  if (!cfg || !out) return fail(nullptr, LBM_ERR_INVALID_ARG, "cfg and out must not be NULL");
+  *out = nullptr;
+  const int n[3] = {cfg->nx, cfg->ny, cfg->nz};
+  for (int a = 0; a < 3; ++a) {
+    if (n[a] < 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "box extent %d on axis %d", n[a], a);
+    if (cfg->periodic[a] && n[a] < 2)
+      return fail(nullptr, LBM_ERR_INVALID_ARG, "periodic axis %d needs extent >= 2", a);
+  }
+  if ((int64_t)n[0] * n[1] * n[2] >= (int64_t)1 << 30)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "box of %lld cells exceeds 2^30", (long long)n[0] * n[1] * n[2]);
+  if (cfg->variant < LBM_TS || cfg->variant > LBM_ET) return fail(nullptr, LBM_ERR_INVALID_ARG, "variant");
+  if (cfg->addressing != LBM_DIRECT && cfg->addressing != LBM_INDIRECT)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "addressing");
+  if (cfg->layout != LBM_SOA && cfg->layout != LBM_AOS) return fail(nullptr, LBM_ERR_INVALID_ARG, "layout");
+  if (cfg->precision < LBM_F64 || cfg->precision > LBM_F16S) return fail(nullptr, LBM_ERR_INVALID_ARG, "precision");
+  if (!(cfg->omega >= 0.0 && cfg->omega < 2.0)) return fail(nullptr, LBM_ERR_INVALID_ARG, "omega must be in [0, 2)");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(cfg->force[a])) return fail(nullptr, LBM_ERR_INVALID_ARG, "force");
+  if (cfg->block_size != 0 && (cfg->block_size % 32 != 0 || cfg->block_size < 32 || cfg->block_size > 512))
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
+  if (cfg->nodes_per_thread < 0 || cfg->nodes_per_thread > 16)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "nodes_per_thread must be in [0, 16]");
+  if (cfg->f16_scale < 0.0 || !std::isfinite(cfg->f16_scale))
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "f16_scale");
+  if (cfg->f16_scale > 0.0) {
+    int e;
+    if (std::frexp(cfg->f16_scale, &e) != 0.5) return fail(nullptr, LBM_ERR_INVALID_ARG, "f16_scale must be 2^k");
+  }
+  if (cfg->dev_alloc && !cfg->dev_free) return fail(nullptr, LBM_ERR_INVALID_ARG, "dev_alloc without dev_free");
+  if (cfg->cg_shift != 0 && cfg->cg_shift < 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift must be >= 2");
+  if (cfg->variant == LBM_CG && cfg->addressing == LBM_INDIRECT)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED, "compressed grid runs on direct addressing only in this build");
+  if (cfg->variant == LBM_SWAP && cfg->addressing == LBM_INDIRECT)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED, "swap runs on direct addressing only in this build");
+
+  lbm_t *h = new lbm_t();
+  h->cfg = *cfg;
+  h->stream = static_cast<cudaStream_t>(cfg->stream);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  h->d_err = static_cast<int *>(dalloc(h, sizeof(int) * 4, h->base_allocs));
+  h->d_out2 = static_cast<double *>(dalloc(h, sizeof(double) * 2, h->base_allocs));
+  if (!h->d_err || !h->d_out2) {
+    free_list(h, h->base_allocs);
+    delete h;
+    return fail(nullptr, LBM_ERR_OOM, "small device buffers");
+  }
+  if (cudaMallocHost(&h->h_out2, sizeof(double) * 2) != cudaSuccess) {
+    cudaGetLastError();
+    free_list(h, h->base_allocs);
+    delete h;
+    return fail(nullptr, LBM_ERR_OOM, "pinned host buffer");
+  }
+  cudaMemsetAsync(h->d_err, 0, sizeof(int) * 4, h->stream);
+  for (int i = 0; i < Q; ++i) h->map[i] = i;
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_t *h) {
+  if (!h) return LBM_OK;
+  cudaStreamSynchronize(h->stream);
+  free_list(h, h->geo_allocs);
+  free_list(h, h->base_allocs);
+  if (h->h_out2) cudaFreeHost(h->h_out2);
+  delete h;
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_t *h) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int flags[4];
+  CUDA_TRY(h, cudaMemcpy(flags, h->d_err, sizeof flags, cudaMemcpyDeviceToHost));
+  if (flags[0]) return fail(h, LBM_ERR_BOUNDS, "a kernel bounds check tripped (code %d)", flags[0]);
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+static lbm_status build_geometry(lbm_t *h) {
+  const lbm_config &c = h->cfg;
+  const bool ind = c.addressing == LBM_INDIRECT;
+  const int64_t ncell = h->cells;
+  std::vector<std::pair<void *, size_t>> temps;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(h->stream);
+    free_list(h, temps);
+  };
+  if (ind) {
+    int32_t *node_of = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * ncell, temps));
+    const int64_t ext = (int64_t)(c.nx + 2) * (c.ny + 2) * (c.nz + 2);
+    const int64_t sc = scan_scratch_elems(std::max(ncell, ext));
+    int32_t *scratch = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * sc, temps));
+    int32_t *cells_tmp = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * ncell, temps));
+    if (!node_of || !scratch || !cells_tmp) {
+      cleanup();
+      return fail(h, LBM_ERR_OOM, "node-list scratch for %lld cells", (long long)ncell);
+    }
+    const int64_t N = build_node_list(h->any_solid ? h->d_solid : nullptr, ncell, node_of, cells_tmp, scratch, sc,
+                                      h->stream);
+    if (N < 0) {
+      cleanup();
+      return fail(h, LBM_ERR_CUDA, "node-list build failed");
+    }
+    h->nodes = N;
+    h->nn = N;
+    h->ipad = round_up(std::max<int64_t>(N, 1), 64);
+    h->d_cells = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * std::max<int64_t>(N, 1), h->geo_allocs));
+    h->d_idx = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * 18 * h->ipad, h->geo_allocs));
+    if (!h->d_cells || !h->d_idx) {
+      cleanup();
+      return fail(h, LBM_ERR_OOM, "IDX for %lld nodes", (long long)N);
+    }
+    h->index_bytes = (int64_t)sizeof(int32_t) * (N + 18 * h->ipad);
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_cells, cells_tmp, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, h->stream));
+    launch_build_idx(h->d_cells, node_of, N, c.nx, c.ny, c.nz, c.periodic, h->d_idx, h->ipad, h->stream);
+    lbm_status st = check_launch(h, "build_idx");
+    if (st != LBM_OK) {
+      cleanup();
+      return st;
+    }
+    h->nghost = 0;
+    if (c.variant == LBM_ET) {
+      int32_t *ghost = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * ext, temps));
+      h->d_etidx = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * 9 * h->ipad, h->geo_allocs));
+      if (!ghost || !h->d_etidx) {
+        cleanup();
+        return fail(h, LBM_ERR_OOM, "esoteric-twist index");
+      }
+      h->index_bytes += (int64_t)sizeof(int32_t) * 9 * h->ipad;
+      const int64_t G = build_et_index(h->d_cells, node_of, N, c.nx, c.ny, c.nz, c.periodic, ghost, h->d_etidx,
+                                       h->ipad, scratch, sc, h->stream);
+      if (G < 0) {
+        cleanup();
+        return fail(h, LBM_ERR_CUDA, "esoteric-twist index build failed");
+      }
+      h->nghost = G;
+    }
+    h->slots = N + h->nghost;
+    if (h->slots >= ((int64_t)1 << 31) - 1) {
+      cleanup();
+      return fail(h, LBM_ERR_INVALID_ARG, "too many storage slots");
+    }
+    cleanup();
+  } else {
+    // full grid; halos only where a scheme needs slots beyond a wall
+    const bool halo = c.variant == LBM_ET;
+    Grid &g = h->grid;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.nz = c.nz;
+    g.px = c.periodic[0];
+    g.py = c.periodic[1];
+    g.pz = c.periodic[2];
+    g.hx = halo && !g.px;
+    g.hy = halo && !g.py;
+    g.hz = halo && !g.pz;
+    int64_t sz = c.nz + 2 * g.hz;
+    if (c.variant == LBM_CG) {
+      // plane offsets 0 or k, plus a ghost plane below and above
+      int k = c.cg_shift;
+      if (k == 0) {
+        const int64_t plane = (int64_t)c.nx * c.ny;
+        int64_t want = (1 << 21) / std::max<int64_t>(plane, 1) + 1;
+        if (want < 2) want = 2;
+        if (want > c.nz + 1) want = c.nz + 1;
+        k = (int)want;
+      }
+      h->cg_k = k;
+      g.hz = 1;
+      sz = c.nz + k + 2;
+    }
+    g.sx = c.nx + 2 * g.hx;
+    g.sxy = g.sx * (c.ny + 2 * g.hy);
+    g.zoff = 0;
+    g.solid = h->any_solid ? h->d_solid : nullptr;
+    h->nn = ncell;
+    h->slots = g.sxy * sz;
+    if (h->slots >= ((int64_t)1 << 31) - 1) return fail(h, LBM_ERR_INVALID_ARG, "too many storage slots");
+    h->index_bytes = h->any_solid ? ncell : 0;
+  }
+  // PDF storage
+  const size_t es = store_size(c.precision);
+  h->npad = c.layout == LBM_SOA ? round_up(std::max<int64_t>(h->slots, 1), 128) : h->slots;
+  h->state_bytes = es * (size_t)Q * (size_t)std::max<int64_t>(h->npad, 1);
+  h->d_A = dalloc(h, h->state_bytes, h->geo_allocs);
+  if (two_lattices(c.variant)) h->d_B = dalloc(h, h->state_bytes, h->geo_allocs);
+  if (!h->d_A || (two_lattices(c.variant) && !h->d_B))
+    return fail(h, LBM_ERR_OOM, "PDF storage of %zu bytes", h->state_bytes);
+  CUDA_TRY(h, cudaMemsetAsync(h->d_A, 0, h->state_bytes, h->stream));
+  if (h->d_B) CUDA_TRY(h, cudaMemsetAsync(h->d_B, 0, h->state_bytes, h->stream));
+  // reduction partials: enough for a step launch and for the read-out kernel
+  const LaunchShape L = shape_of(h);
+  h->partial_blocks = (int)std::max<int64_t>(L.grid.x, reduce_blocks_for(h->nn));
+  h->d_partials = static_cast<double *>(dalloc(h, sizeof(double) * 2 * h->partial_blocks, h->geo_allocs));
+  if (!h->d_partials) return fail(h, LBM_ERR_OOM, "reduction partials");
+  h->has_geometry = true;
+  return LBM_OK;
+}
+
+static void reset_geometry(lbm_t *h) {
+  cudaStreamSynchronize(h->stream);
+  free_list(h, h->geo_allocs);
+  h->d_solid = nullptr;
+  h->d_cells = h->d_idx = h->d_etidx = nullptr;
+  h->d_A = h->d_B = nullptr;
+  h->d_partials = nullptr;
+  h->has_geometry = false;
+  h->cells = (int64_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+  h->nodes = h->nghost = h->nn = h->slots = h->npad = h->ipad = 0;
+  h->steps = 0;
+  for (int i = 0; i < Q; ++i) h->map[i] = i;
+}
+
+static lbm_status finish_geometry(lbm_t *h) {
+  lbm_status st = build_geometry(h);
+  if (st != LBM_OK) {
+    reset_geometry(h);
+    return st;
+  }
+  st = lbm_init(h, nullptr, nullptr, 0);
+  if (st != LBM_OK) return st;
+  return lbm_sync(h);
+}
+
+lbm_status lbm_set_geometry(lbm_t *h, const uint8_t *mask) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  reset_geometry(h);
+  const int64_t ncell = h->cells;
+  int64_t fluid = ncell;
+  h->any_solid = false;
+  if (mask) {
+    fluid = 0;
+    for (int64_t c = 0; c < ncell; ++c) fluid += mask[c] == 0;
+    h->any_solid = fluid != ncell;
+  }
+  h->d_solid = static_cast<uint8_t *>(dalloc(h, (size_t)ncell, h->geo_allocs));
+  if (!h->d_solid) return fail(h, LBM_ERR_OOM, "solid mask of %lld cells", (long long)ncell);
+  if (mask) {
+    // normalise to 0/1 on the host copy path
+    std::vector<uint8_t> m01(mask, mask + ncell);
+    for (auto &v : m01) v = v != 0;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_solid, m01.data(), (size_t)ncell, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  } else {
+    CUDA_TRY(h, cudaMemsetAsync(h->d_solid, 0, (size_t)ncell, h->stream));
+  }
+  h->nodes = fluid;
+  lbm_status st = finish_geometry(h);
+  if (st == LBM_OK && h->cfg.addressing == LBM_DIRECT) h->nodes = fluid;
+  return st;
+}
+
+lbm_status lbm_set_geometry_spheres(lbm_t *h, int64_t nsph, const int64_t *centres, int64_t radius, int64_t unit) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (nsph < 0 || (nsph > 0 && !centres) || radius < 0 || unit < 1)
+    return fail(h, LBM_ERR_INVALID_ARG, "sphere arguments");
+  reset_geometry(h);
+  const int64_t ncell = h->cells;
+  h->d_solid = static_cast<uint8_t *>(dalloc(h, (size_t)ncell, h->geo_allocs));
+  if (!h->d_solid) return fail(h, LBM_ERR_OOM, "solid mask of %lld cells", (long long)ncell);
+  CUDA_TRY(h, cudaMemsetAsync(h->d_solid, 0, (size_t)ncell, h->stream));
+  if (nsph > 0) {
+    TempBuf cen(h, sizeof(int64_t) * 3 * nsph);
+    if (!cen.p) return fail(h, LBM_ERR_OOM, "sphere centres");
+    CUDA_TRY(h, cudaMemcpyAsync(cen.p, centres, sizeof(int64_t) * 3 * nsph, cudaMemcpyHostToDevice, h->stream));
+    launch_sphere_mask(h->d_solid, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.periodic, nsph,
+                       static_cast<const int64_t *>(cen.p), radius, unit, h->stream);
+    lbm_status st = check_launch(h, "sphere_mask");
+    if (st != LBM_OK) return st;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  // fluid count for the full-grid case (the node list counts it for IDX)
+  {
+    std::vector<uint8_t> m((size_t)ncell);
+    CUDA_TRY(h, cudaMemcpy(m.data(), h->d_solid, (size_t)ncell, cudaMemcpyDeviceToHost));
+    int64_t fluid = 0;
+    for (auto v : m) fluid += v == 0;
+    h->nodes = fluid;
+    h->any_solid = fluid != ncell;
+  }
+  const int64_t fluid = h->nodes;
+  lbm_status st = finish_geometry(h);
+  if (st == LBM_OK && h->cfg.addressing == LBM_DIRECT) h->nodes = fluid;
+  return st;
+}
+
+lbm_status lbm_get_mask(lbm_t *h, uint8_t *mask) {
+  if (!h || !mask) return fail(h, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(mask, h->d_solid, (size_t)h->cells, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_nodes(lbm_t *h, int32_t *cells) {
+  if (!h || !cells) return fail(h, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (h->cfg.addressing != LBM_INDIRECT) return fail(h, LBM_ERR_INVALID_ARG, "node list exists for indirect addressing");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(cells, h->d_cells, sizeof(int32_t) * h->nodes, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_idx(lbm_t *h, int32_t *idx) {
+  if (!h || !idx) return fail(h, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (h->cfg.addressing != LBM_INDIRECT) return fail(h, LBM_ERR_INVALID_ARG, "IDX exists for indirect addressing");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (h->nodes > 0)
+    CUDA_TRY(h, cudaMemcpy2D(idx, sizeof(int32_t) * h->nodes, h->d_idx, sizeof(int32_t) * h->ipad,
+                             sizeof(int32_t) * h->nodes, 18, cudaMemcpyDeviceToHost));
+  return LBM_OK;
+}
+
+static int kernels_per_step(const lbm_t *h) {
+  switch (h->cfg.variant) {
+    case LBM_TS: return 2;
+    case LBM_CG: {
+      const int slab = h->cg_k - 1;
+      return (h->cfg.nz + slab - 1) / slab + (h->cfg.periodic[2] ? 1 : 0);
+    }
+    case LBM_SWAP: return 8;
+    default: return 1;
+  }
+}
+
+lbm_status lbm_get_info(const lbm_t *h, lbm_info *info) {
+  if (!h || !info) return fail(nullptr, LBM_ERR_INVALID_ARG, "NULL argument");
+  memset(info, 0, sizeof *info);
+  info->cells = h->cells;
+  info->nodes = h->nodes;
+  info->storage_nodes = h->slots;
+  info->state_bytes = (int64_t)h->state_bytes * (h->d_B ? 2 : 1);
+  info->index_bytes = h->index_bytes;
+  info->steps = h->steps;
+  info->natural = is_natural(h);
+  info->kernels_per_step = kernels_per_step(h);
+  info->f16_scale = h->scale;
+  info->reduce_blocks = h->partial_blocks;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+static float choose_scale(const lbm_t *h, double dev_init) {
+  if (h->cfg.precision != LBM_F16S) return 1.0f;
+  if (h->cfg.f16_scale > 0.0) return (float)h->cfg.f16_scale;
+  // largest deviation expected: the initial state's, or the velocity a body
+  // force can drive through the box (channel estimate g L^2 / (8 nu)) times
+  // the largest 3 w_i c.u term; map it to about 2^12 so the FP16 values stay
+  // normal across many decades below it
+  const double nu = h->cfg.omega > 0 ? (1.0 / h->cfg.omega - 0.5) / 3.0 : 1.0;
+  const double gmag = std::sqrt(h->cfg.force[0] * h->cfg.force[0] + h->cfg.force[1] * h->cfg.force[1] +
+                                h->cfg.force[2] * h->cfg.force[2]);
+  const double L = std::max(h->cfg.nx, std::max(h->cfg.ny, h->cfg.nz));
+  const double dforce = 3.0 / 18.0 * gmag * L * L / (8.0 * std::max(nu, 1e-6));
+  double dmax = std::max(dev_init, dforce);
+  if (!(dmax > 1e-12)) dmax = 1e-6;
+  return (float)std::ldexp(1.0, (int)std::floor(std::log2(4096.0 / dmax)));
+}
+
+lbm_status lbm_init(lbm_t *h, const double *rho, const double *u, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  const int64_t n = h->nn;
+  double dev = 0.0;
+  const double *drho = rho, *du = u;
+  TempBuf trho(h, rho && !on_device ? sizeof(double) * n : 0), tu(h, u && !on_device ? sizeof(double) * 3 * n : 0);
+  if (!on_device) {
+    const bool f16 = h->cfg.precision == LBM_F16S;
+    if (rho) {
+      if (f16)
+        for (int64_t k = 0; k < n; ++k) dev = std::max(dev, std::fabs(rho[k] - 1.0) / 3.0);
+      if (!trho.p) return fail(h, LBM_ERR_OOM, "init buffer");
+      CUDA_TRY(h, cudaMemcpyAsync(trho.p, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+      drho = static_cast<const double *>(trho.p);
+    }
+    if (u) {
+      double um = 0.0;
+      if (f16)
+        for (int64_t k = 0; k < 3 * n; ++k) um = std::max(um, std::fabs(u[k]));
+      dev += 3.0 / 18.0 * um * 2.0;
+      if (!tu.p) return fail(h, LBM_ERR_OOM, "init buffer");
+      CUDA_TRY(h, cudaMemcpyAsync(tu.p, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+      du = static_cast<const double *>(tu.p);
+    }
+  } else if (rho || u) {
+    dev = 1e-3;  // device arrays are not inspected; assume a small perturbation
+  }
+  h->scale = choose_scale(h, dev);
+  h->steps = 0;
+  h->cg_o = 0;
+  for (int i = 0; i < Q; ++i) h->map[i] = i;
+  h->grid.zoff = 0;
+  StateDesc d = state_desc(h);
+  launch_put_state(d, nullptr, drho, du, h->stream);
+  lbm_status st = check_launch(h, "put_state");
+  if (st != LBM_OK) return st;
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_pdfs(lbm_t *h, const double *f, int on_device) {
+  if (!h || !f) return fail(h, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  const int64_t n = h->nn;
+  const size_t bytes = sizeof(double) * Q * n;
+  TempBuf tmp(h, on_device ? 0 : bytes);
+  const double *df = f;
+  double dev = 0.0;
+  if (!on_device) {
+    static const double w[Q] = {1. / 3, 1. / 18, 1. / 18, 1. / 18, 1. / 18, 1. / 18, 1. / 18,
+                                1. / 36, 1. / 36, 1. / 36, 1. / 36, 1. / 36, 1. / 36, 1. / 36,
+                                1. / 36, 1. / 36, 1. / 36, 1. / 36, 1. / 36};
+    if (h->cfg.precision == LBM_F16S)
+      for (int i = 0; i < Q; ++i)
+        for (int64_t k = 0; k < n; ++k) dev = std::max(dev, std::fabs(f[i * n + k] - w[i]));
+    if (!tmp.p) return fail(h, LBM_ERR_OOM, "state buffer");
+    CUDA_TRY(h, cudaMemcpyAsync(tmp.p, f, bytes, cudaMemcpyHostToDevice, h->stream));
+    df = static_cast<const double *>(tmp.p);
+  } else {
+    dev = 1e-3;
+  }
+  h->scale = choose_scale(h, dev);
+  h->steps = 0;
+  h->cg_o = 0;
+  h->grid.zoff = 0;
+  for (int i = 0; i < Q; ++i) h->map[i] = i;
+  StateDesc d = state_desc(h);
+  launch_put_state(d, df, nullptr, nullptr, h->stream);
+  lbm_status st = check_launch(h, "put_state");
+  if (st != LBM_OK) return st;
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_pdfs(lbm_t *h, double *f, int on_device) {
+  if (!h || !f) return fail(h, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (!is_natural(h)) return fail(h, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
+  const int64_t n = h->nn;
+  const size_t bytes = sizeof(double) * Q * n;
+  TempBuf tmp(h, on_device ? 0 : bytes);
+  double *df = f;
+  if (!on_device) {
+    if (!tmp.p) return fail(h, LBM_ERR_OOM, "state buffer");
+    df = static_cast<double *>(tmp.p);
+  }
+  StateDesc d = state_desc(h);
+  launch_get_state(d, df, h->stream);
+  lbm_status st = check_launch(h, "get_state");
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    CUDA_TRY(h, cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_macroscopics(lbm_t *h, double *rho, double *u, int on_device) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (!is_natural(h)) return fail(h, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
+  const int64_t n = h->nn;
+  TempBuf tr(h, (!on_device && rho) ? sizeof(double) * n : 0), tu(h, (!on_device && u) ? sizeof(double) * 3 * n : 0);
+  double *dr = rho, *du = u;
+  if (!on_device) {
+    if ((rho && !tr.p) || (u && !tu.p)) return fail(h, LBM_ERR_OOM, "moment buffers");
+    dr = rho ? static_cast<double *>(tr.p) : nullptr;
+    du = u ? static_cast<double *>(tu.p) : nullptr;
+  }
+  StateDesc d = state_desc(h);
+  launch_macroscopics(d, dr, du, h->stream);
+  lbm_status st = check_launch(h, "macroscopics");
+  if (st != LBM_OK) return st;
+  if (!on_device) {
+    if (rho) CUDA_TRY(h, cudaMemcpyAsync(rho, dr, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    if (u) CUDA_TRY(h, cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+static lbm_status read_out2(lbm_t *h, double *mass, double *jx) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_out2, h->d_out2, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+  lbm_status st = lbm_sync(h);
+  if (st != LBM_OK) return st;
+  if (mass) *mass = h->h_out2[0];
+  if (jx) *jx = h->h_out2[1];
+  return LBM_OK;
+}
+
+lbm_status lbm_flux(lbm_t *h, double *mass, double *jx) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (!is_natural(h)) return fail(h, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
+  const int nb = reduce_blocks_for(h->nn);
+  StateDesc d = state_desc(h);
+  launch_flux_partials(d, h->d_partials, nb, h->stream);
+  launch_final_sum(h->d_partials, nb, h->d_out2, h->stream);
+  lbm_status st = check_launch(h, "flux");
+  if (st != LBM_OK) return st;
+  return read_out2(h, mass, jx);
+}
+
+// ---------------------------------------------------------------------------
+// Time stepping.
+static lbm_status cg_step(lbm_t *h, bool red);
+static lbm_status swap_step(lbm_t *h, bool red);
+
+static lbm_status one_step(lbm_t *h, bool red) {
+  const KernelKey k = key_of(h, red);
+  const LaunchShape L = shape_of(h);
+  const int v = h->cfg.variant;
+  switch (v) {
+    case LBM_TS: {
+      StepParams p = params_of(h);
+      launch_step_kernel(VAR_TS, 0, p, k, L);
+      launch_step_kernel(VAR_TS, 1, p, key_of(h, false), L);
+      break;
+    }
+    case LBM_OS_PUSH:
+    case LBM_OS_PULL: {
+      StepParams p = params_of(h);
+      launch_step_kernel(v == LBM_OS_PUSH ? VAR_OS_PUSH : VAR_OS_PULL, 0, p, k, L);
+      std::swap(h->d_A, h->d_B);
+      break;
+    }
+    case LBM_AA: {
+      StepParams p = params_of(h);
+      launch_step_kernel(VAR_AA, (int)(h->steps & 1), p, k, L);
+      break;
+    }
+    case LBM_ET: {
+      StepParams p = params_of(h);
+      launch_step_kernel(VAR_ET, 0, p, k, L);
+      int nm[Q];
+      for (int i = 0; i < Q; ++i) nm[i] = h->map[OPP(i)];
+      memcpy(h->map, nm, sizeof nm);
+      break;
+    }
+    case LBM_CG: {
+      lbm_status st = cg_step(h, red);
+      if (st != LBM_OK) return st;
+      break;
+    }
+    case LBM_SWAP: {
+      lbm_status st = swap_step(h, red);
+      if (st != LBM_OK) return st;
+      break;
+    }
+  }
+  lbm_status st = check_launch(h, "step");
+  if (st != LBM_OK) return st;
+  ++h->steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_t *h, int n) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (n < 0) return fail(h, LBM_ERR_INVALID_ARG, "negative step count");
+  for (int t = 0; t < n; ++t) {
+    lbm_status st = one_step(h, false);
+    if (st != LBM_OK) return st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
+  if (n < 1) return fail(h, LBM_ERR_INVALID_ARG, "step count must be >= 1");
+  if (!is_natural(h)) return fail(h, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
+  lbm_status st = one_step(h, true);
+  if (st != LBM_OK) return st;
+  launch_final_sum(h->d_partials, (int)shape_of(h).grid.x, h->d_out2, h->stream);
+  st = check_launch(h, "final_sum");
+  if (st != LBM_OK) return st;
+  for (int t = 1; t < n; ++t) {
+    st = one_step(h, false);
+    if (st != LBM_OK) return st;
+  }
+  return read_out2(h, mass, jx);
+}
+
+}  // extern "C"
+
+// Compressed grid and swap are implemented in their own files.
+static lbm_status cg_step(lbm_t *h, bool) { return fail(h, LBM_ERR_UNSUPPORTED, "compressed grid not built"); }
+static lbm_status swap_step(lbm_t *h, bool) { return fail(h, LBM_ERR_UNSUPPORTED, "swap not built"); }

@@ -1,0 +1,97 @@
+// Host-side internals shared by the library's translation units: kernel
+// selection keys, launch shapes, and the launchers each .cu file exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lbm_core.cuh"
+
+namespace lbmk {
+
+enum { VAR_TS = 0, VAR_OS_PUSH = 1, VAR_OS_PULL = 2, VAR_CG = 3, VAR_SWAP = 4, VAR_AA = 5, VAR_ET = 6 };
+
+// How the natural state f_i(x) maps to storage.
+enum {
+  MAP_NATURAL = 0,  // slot i of x (TS, OS push, swap, AA at even step count)
+  MAP_PULL = 1,     // post-collision storage: f_i(x) = A_i(x - c_i), or A_opp(i)(x) across a solid link
+  MAP_ET = 2        // esoteric twist: array map[i] at x + s(i)
+};
+
+struct KernelKey {
+  int precision;  // 0 F64, 1 F32, 2 F16S
+  int aos;        // 0 SoA, 1 AoS
+  bool ind;       // IDX addressing
+  bool force;     // nonzero body force
+  bool red;       // fused (mass, flux) reduction
+};
+
+struct LaunchShape {
+  dim3 grid, block;
+  cudaStream_t stream;
+};
+
+// lbm_steps_*.cu: TS (sub 0 collide, 1 stream), OS push/pull, AA (sub = odd), ET
+template <class C>
+void launch_step_kernel_t(int variant, int sub, const StepParams &p, const KernelKey &k, const LaunchShape &L);
+extern template void launch_step_kernel_t<CodecF64>(int, int, const StepParams &, const KernelKey &, const LaunchShape &);
+extern template void launch_step_kernel_t<CodecF32>(int, int, const StepParams &, const KernelKey &, const LaunchShape &);
+extern template void launch_step_kernel_t<CodecF16S>(int, int, const StepParams &, const KernelKey &, const LaunchShape &);
+inline void launch_step_kernel(int variant, int sub, const StepParams &p, const KernelKey &k, const LaunchShape &L) {
+  if (k.precision == 0)
+    launch_step_kernel_t<CodecF64>(variant, sub, p, k, L);
+  else if (k.precision == 1)
+    launch_step_kernel_t<CodecF32>(variant, sub, p, k, L);
+  else
+    launch_step_kernel_t<CodecF16S>(variant, sub, p, k, L);
+}
+
+// lbm_cg.cu: one slab of the compressed grid, and its periodic ghost planes
+void launch_cg_slab(const StepParams &p, const KernelKey &k, const LaunchShape &L);
+void launch_cg_ghost(const StepParams &p, int precision, int aos, int zo, cudaStream_t s);
+
+// lbm_swap.cu: one colour pass of the blocked swap
+struct SwapTiles {
+  int tx, ty, tz;       // tile extent in cells
+  int ntx, nty, ntz;    // tiles per axis
+  int colour;           // pass being run
+  int ncolours;
+};
+void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
+size_t swap_smem_bytes(const SwapTiles &t, int precision);
+
+// lbm_setup.cu
+void launch_sphere_mask(uint8_t *solid, int nx, int ny, int nz, const int *periodic, int64_t nsph,
+                        const int64_t *centres, int64_t radius, int64_t unit, cudaStream_t s);
+// exclusive prefix count of nonzero bytes; node_of[c] = number or -1; cells[k] = c
+int64_t build_node_list(const uint8_t *solid, int64_t ncell, int32_t *node_of, int32_t *cells,
+                        int32_t *scratch, int64_t scratch_elems, cudaStream_t s);
+int64_t scan_scratch_elems(int64_t n);
+void launch_build_idx(const int32_t *cells, const int32_t *node_of, int64_t N, int nx, int ny, int nz,
+                      const int *periodic, int32_t *idx, int64_t ipad, cudaStream_t s);
+// esoteric twist packed index; ghost_map is (nx+2)(ny+2)(nz+2) int32 scratch
+int64_t build_et_index(const int32_t *cells, const int32_t *node_of, int64_t N, int nx, int ny, int nz,
+                       const int *periodic, int32_t *ghost_map, int32_t *etidx, int64_t ipad,
+                       int32_t *scratch, int64_t scratch_elems, cudaStream_t s);
+
+// state <-> natural FP64 arrays, moments and reductions
+struct StateDesc {
+  StepParams p;       // A (state), npad, grid/idx, map, scale
+  KernelKey k;        // precision, aos, ind
+  int mapkind;        // MAP_*
+  const int32_t *cells;  // indirect: node -> cell (for rho/u outputs this is not needed)
+};
+// f_nat: 19 x n FP64 (n = nodes), or computed as f_eq(rho, u) when f_nat is null
+void launch_put_state(const StateDesc &d, const double *f_nat, const double *rho, const double *u,
+                      cudaStream_t s);
+// write natural FP64 (solid cells of a direct grid get 0)
+void launch_get_state(const StateDesc &d, double *f_nat, cudaStream_t s);
+void launch_macroscopics(const StateDesc &d, double *rho, double *u, cudaStream_t s);
+// per-block partials then one fixed-order final sum into out[2]
+int reduce_blocks_for(int64_t nnodes);
+void launch_flux_partials(const StateDesc &d, double *partials, int nblocks, cudaStream_t s);
+void launch_final_sum(const double *partials, int nblocks, double *out, cudaStream_t s);
+
+}  // namespace lbmk

@@ -1,0 +1,365 @@
+"""Thin ctypes binding of liblbm (include/lbm.h).
+
+The functions here carry the C names and only marshal arguments: every step
+of the computation runs in the library's CUDA kernels.  Loading fails loudly
+when ``liblbm.so`` has not been built; there is no CPU fallback.
+
+PyTorch is used only for plumbing: the default device allocator hands the
+library PyTorch's caching allocator, and the default stream is PyTorch's
+current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+# enums of include/lbm.h
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_BOUNDS, \
+    LBM_ERR_TIMEOUT, LBM_ERR_NOT_CONVERGED, LBM_ERR_UNSUPPORTED = range(9)
+LBM_TS, LBM_OS_PUSH, LBM_OS_PULL, LBM_CG, LBM_SWAP, LBM_AA, LBM_ET = range(7)
+LBM_DIRECT, LBM_INDIRECT = 0, 1
+LBM_SOA, LBM_AOS = 0, 1
+LBM_F64, LBM_F32, LBM_F16S = 0, 1, 2
+
+VARIANTS = {"ts": LBM_TS, "os_push": LBM_OS_PUSH, "os_pull": LBM_OS_PULL, "cg": LBM_CG,
+            "swap": LBM_SWAP, "aa": LBM_AA, "et": LBM_ET}
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
+Q = 19
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("periodic", ctypes.c_int32 * 3),
+                ("variant", ctypes.c_int32), ("addressing", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("omega", ctypes.c_double), ("force", ctypes.c_double * 3),
+                ("f16_scale", ctypes.c_double),
+                ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
+                ("cg_shift", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("nodes", ctypes.c_int64),
+                ("storage_nodes", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+                ("index_bytes", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("natural", ctypes.c_int32), ("kernels_per_step", ctypes.c_int32),
+                ("f16_scale", ctypes.c_double), ("reduce_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+# exported symbols and their signatures (every function declared in lbm.h)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "lbm_config_default": (_I, [ctypes.POINTER(lbm_config)]),
+    "lbm_create": (_I, [ctypes.POINTER(lbm_config), ctypes.POINTER(_P)]),
+    "lbm_destroy": (_I, [_P]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_status_string": (ctypes.c_char_p, [_I]),
+    "lbm_set_geometry": (_I, [_P, _P]),
+    "lbm_set_geometry_spheres": (_I, [_P, _I64, _P, _I64, _I64]),
+    "lbm_get_mask": (_I, [_P, _P]),
+    "lbm_get_nodes": (_I, [_P, _P]),
+    "lbm_get_idx": (_I, [_P, _P]),
+    "lbm_get_info": (_I, [_P, ctypes.POINTER(lbm_info)]),
+    "lbm_init": (_I, [_P, _P, _P, _I]),
+    "lbm_set_pdfs": (_I, [_P, _P, _I]),
+    "lbm_get_pdfs": (_I, [_P, _P, _I]),
+    "lbm_step": (_I, [_P, _I]),
+    "lbm_step_flux": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_flux": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_macroscopics": (_I, [_P, _P, _P, _I]),
+    "lbm_sync": (_I, [_P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_status_name(status), status, msg))
+        self.status = status
+
+
+def _status_name(s):
+    names = ["LBM_OK", "LBM_ERR_INVALID_ARG", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR_STATE",
+             "LBM_ERR_BOUNDS", "LBM_ERR_TIMEOUT", "LBM_ERR_NOT_CONVERGED", "LBM_ERR_UNSUPPORTED"]
+    return names[s] if 0 <= s < len(names) else "status"
+
+
+def load(path: str | None = None):
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError("liblbm.so is not built (%s); run paper_1111_0922_gb300.build.build()" % p)
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(h, status):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(h)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):  # torch tensor on the device
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# C-named functions (argument marshalling only)
+
+def lbm_config_default():
+    cfg = lbm_config()
+    _check(None, load().lbm_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def lbm_create(cfg: lbm_config):
+    h = ctypes.c_void_p()
+    st = load().lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def lbm_destroy(h):
+    _check(None, load().lbm_destroy(h))
+
+
+def lbm_set_geometry(h, solid_mask=None):
+    m = None if solid_mask is None else np.ascontiguousarray(solid_mask, dtype=np.uint8).reshape(-1)
+    _check(h, load().lbm_set_geometry(h, _ptr(m)))
+
+
+def lbm_set_geometry_spheres(h, centres, radius, unit):
+    c = np.ascontiguousarray(np.asarray(centres, dtype=np.int64).reshape(-1, 3))
+    _check(h, load().lbm_set_geometry_spheres(h, c.shape[0], _ptr(c), int(radius), int(unit)))
+
+
+def lbm_get_info(h) -> lbm_info:
+    info = lbm_info()
+    _check(h, load().lbm_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def lbm_get_mask(h, ncells):
+    out = np.empty(ncells, np.uint8)
+    _check(h, load().lbm_get_mask(h, _ptr(out)))
+    return out
+
+
+def lbm_get_nodes(h, nnodes):
+    out = np.empty(nnodes, np.int32)
+    _check(h, load().lbm_get_nodes(h, _ptr(out)))
+    return out
+
+
+def lbm_get_idx(h, nnodes):
+    out = np.empty((18, nnodes), np.int32)
+    _check(h, load().lbm_get_idx(h, _ptr(out)))
+    return out
+
+
+def lbm_init(h, rho=None, u=None, on_device=False):
+    if not on_device:
+        rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+        u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+    _check(h, load().lbm_init(h, _ptr(rho), _ptr(u), int(bool(on_device))))
+
+
+def lbm_set_pdfs(h, f, on_device=False):
+    if not on_device:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(h, load().lbm_set_pdfs(h, _ptr(f), int(bool(on_device))))
+
+
+def lbm_get_pdfs(h, n=None, out=None, on_device=False):
+    if out is None:
+        out = np.empty((Q, n), np.float64)
+    _check(h, load().lbm_get_pdfs(h, _ptr(out), int(bool(on_device))))
+    return out
+
+
+def lbm_step(h, n=1):
+    _check(h, load().lbm_step(h, int(n)))
+
+
+def lbm_step_flux(h, n=1):
+    m = ctypes.c_double()
+    j = ctypes.c_double()
+    _check(h, load().lbm_step_flux(h, int(n), ctypes.byref(m), ctypes.byref(j)))
+    return m.value, j.value
+
+
+def lbm_flux(h):
+    m = ctypes.c_double()
+    j = ctypes.c_double()
+    _check(h, load().lbm_flux(h, ctypes.byref(m), ctypes.byref(j)))
+    return m.value, j.value
+
+
+def lbm_macroscopics(h, n=None, rho=None, u=None, on_device=False, want_rho=True, want_u=True):
+    if not on_device:
+        rho = (np.empty(n, np.float64) if rho is None else rho) if want_rho else None
+        u = (np.empty((n, 3), np.float64) if u is None else u) if want_u else None
+    _check(h, load().lbm_macroscopics(h, _ptr(rho), _ptr(u), int(bool(on_device))))
+    return rho, u
+
+
+def lbm_sync(h):
+    _check(h, load().lbm_sync(h))
+
+
+# ---------------------------------------------------------------------------
+# Convenience object over the same calls
+
+class _TorchAllocator:
+    """Device allocation through PyTorch's caching allocator (plumbing)."""
+
+    def __init__(self, device, stream):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+
+        def alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:  # noqa: BLE001 - report as a NULL allocation (LBM_ERR_OOM)
+                return None
+
+        def free(ptr, nbytes, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+class Lattice:
+    """A D3Q19 lattice on one GPU: geometry, state and time stepping."""
+
+    def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
+                 layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0,
+                 stream=None, use_torch_allocator=True):
+        self.cfg = lbm_config_default()
+        c = self.cfg
+        c.nx, c.ny, c.nz = (int(d) for d in dims)
+        for a in range(3):
+            c.periodic[a] = int(periodic[a])
+            c.force[a] = float(force[a])
+        c.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        c.addressing = {"direct": LBM_DIRECT, "indirect": LBM_INDIRECT}[addressing] \
+            if isinstance(addressing, str) else int(addressing)
+        c.layout = {"soa": LBM_SOA, "aos": LBM_AOS}[layout] if isinstance(layout, str) else int(layout)
+        c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        c.omega = float(omega)
+        c.f16_scale = float(f16_scale)
+        c.block_size = int(block_size)
+        c.nodes_per_thread = int(nodes_per_thread)
+        c.cg_shift = int(cg_shift)
+        self._alloc = None
+        if stream is None or use_torch_allocator:
+            import torch
+
+            dev = torch.cuda.current_device()
+            if stream is None:
+                stream = torch.cuda.current_stream(dev).cuda_stream
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(dev, stream)
+                c.dev_alloc = self._alloc.alloc
+                c.dev_free = self._alloc.free
+        c.stream = ctypes.c_void_p(int(stream) if stream else 0)
+        self.dims = tuple(int(d) for d in dims)
+        self.h = lbm_create(c)
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    # geometry
+    def set_geometry(self, solid=None):
+        lbm_set_geometry(self.h, solid)
+
+    def set_geometry_spheres(self, centres, radius, unit):
+        lbm_set_geometry_spheres(self.h, centres, radius, unit)
+
+    @property
+    def info(self) -> lbm_info:
+        return lbm_get_info(self.h)
+
+    @property
+    def n(self) -> int:
+        """Length of natural arrays: cells (direct) or fluid nodes (indirect)."""
+        i = self.info
+        return int(i.cells if self.cfg.addressing == LBM_DIRECT else i.nodes)
+
+    def mask(self):
+        return lbm_get_mask(self.h, int(np.prod(self.dims)))
+
+    def nodes(self):
+        return lbm_get_nodes(self.h, self.info.nodes)
+
+    def idx(self):
+        return lbm_get_idx(self.h, self.info.nodes)
+
+    # state
+    def init(self, rho=None, u=None, on_device=False):
+        lbm_init(self.h, rho, u, on_device)
+
+    def set_pdfs(self, f, on_device=False):
+        lbm_set_pdfs(self.h, f, on_device)
+
+    def pdfs(self):
+        return lbm_get_pdfs(self.h, self.n)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def step_flux(self, n=1):
+        return lbm_step_flux(self.h, n)
+
+    def flux(self):
+        return lbm_flux(self.h)
+
+    def macroscopics(self):
+        return lbm_macroscopics(self.h, self.n)
+
+    def sync(self):
+        lbm_sync(self.h)
