@@ -2,6 +2,7 @@
 // set-up, state in/out, time stepping and reductions.  Host code only; every
 // step of the path runs in the kernels of lbm_steps.cu, lbm_cg.cu,
 // lbm_swap.cu and lbm_setup.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -182,6 +183,19 @@ static LaunchShape shape_of(const lbm_t *h) {
   L.block = dim3((unsigned)bs);
   L.stream = h->stream;
   return L;
+}
+
+static SwapTiles swap_tiles(const lbm_t *h) {
+  SwapTiles t;
+  t.tx = std::min(32, h->cfg.nx);
+  t.ty = std::min(4, h->cfg.ny);
+  t.tz = std::min(4, h->cfg.nz);
+  t.ntx = (h->cfg.nx + t.tx - 1) / t.tx;
+  t.nty = (h->cfg.ny + t.ty - 1) / t.ty;
+  t.ntz = (h->cfg.nz + t.tz - 1) / t.tz;
+  t.colour = 0;
+  t.ncolours = swap_colours(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]);
+  return t;
 }
 
 static StateDesc state_desc(const lbm_t *h) {
@@ -422,7 +436,13 @@ static lbm_status build_geometry(lbm_t *h) {
   if (h->d_B) CUDA_TRY(h, cudaMemsetAsync(h->d_B, 0, h->state_bytes, h->stream));
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
-  h->partial_blocks = (int)std::max<int64_t>(L.grid.x, reduce_blocks_for(h->nn));
+  int64_t need = std::max<int64_t>(L.grid.x, reduce_blocks_for(h->nn));
+  if (c.variant == LBM_CG) need += (c.nz + h->cg_k - 2) / (h->cg_k - 1) + 1;  // one partial tile per slab
+  if (c.variant == LBM_SWAP) {
+    const SwapTiles t = swap_tiles(h);
+    need = std::max<int64_t>(need, (int64_t)t.ntx * t.nty * t.ntz);
+  }
+  h->partial_blocks = (int)need;
   h->d_partials = static_cast<double *>(dalloc(h, sizeof(double) * 2 * h->partial_blocks, h->geo_allocs));
   if (!h->d_partials) return fail(h, LBM_ERR_OOM, "reduction partials");
   h->has_geometry = true;
@@ -551,7 +571,7 @@ static int kernels_per_step(const lbm_t *h) {
       const int slab = h->cg_k - 1;
       return (h->cfg.nz + slab - 1) / slab + (h->cfg.periodic[2] ? 1 : 0);
     }
-    case LBM_SWAP: return 8;
+    case LBM_SWAP: return swap_tiles(h).ncolours;
     default: return 1;
   }
 }
@@ -736,10 +756,66 @@ lbm_status lbm_flux(lbm_t *h, double *mass, double *jx) {
 
 // ---------------------------------------------------------------------------
 // Time stepping.
-static lbm_status cg_step(lbm_t *h, bool red);
-static lbm_status swap_step(lbm_t *h, bool red);
 
-static lbm_status one_step(lbm_t *h, bool red) {
+// Compressed grid: ghost planes (periodic z), then slabs of k-1 planes in
+// the order that keeps every overwritten plane's readers in earlier slabs.
+// Returns the number of reduction partials written when red.
+static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
+  const KernelKey k = key_of(h, red);
+  StepParams p = params_of(h);
+  const int o_old = h->cg_o, o_new = o_old == 0 ? h->cg_k : 0;
+  if (h->cfg.periodic[2]) launch_cg_ghost(p, h->cfg.precision, h->cfg.layout == LBM_AOS, o_old, h->stream);
+  const int slab = h->cg_k - 1, nz = h->cfg.nz;
+  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 256;
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
+  const int64_t plane = (int64_t)h->cfg.nx * h->cfg.ny;
+  p.zo_read = o_old;
+  p.zo_write = o_new;
+  int used = 0;
+  const int nslab = (nz + slab - 1) / slab;
+  for (int s = 0; s < nslab; ++s) {
+    int z0, z1;
+    if (o_new > o_old) {  // descending
+      z1 = nz - s * slab;
+      z0 = std::max(0, z1 - slab);
+    } else {
+      z0 = s * slab;
+      z1 = std::min(nz, z0 + slab);
+    }
+    p.z0 = z0;
+    p.z1 = z1;
+    LaunchShape L;
+    const int64_t cnt = plane * (z1 - z0);
+    L.grid = dim3((unsigned)std::max<int64_t>(1, (cnt + (int64_t)bs * npt - 1) / ((int64_t)bs * npt)));
+    L.block = dim3(bs);
+    L.stream = h->stream;
+    p.partials = h->d_partials + 2 * used;
+    launch_step_kernel_cg(p, k, L);
+    used += (int)L.grid.x;
+  }
+  h->cg_o = o_new;
+  h->grid.zoff = o_new;
+  if (red_blocks) *red_blocks = used;
+  return LBM_OK;
+}
+
+static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
+  const KernelKey k = key_of(h, red);
+  StepParams p = params_of(h);
+  SwapTiles t = swap_tiles(h);
+  int used = 0;
+  for (int c = 0; c < t.ncolours; ++c) {
+    t.colour = c;
+    p.partials = h->d_partials + 2 * used;
+    launch_swap_pass(p, t, k, h->stream);
+    used += swap_blocks(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2], c);
+  }
+  if (red_blocks) *red_blocks = used;
+  return LBM_OK;
+}
+
+static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
+  if (red_blocks) *red_blocks = (int)shape_of(h).grid.x;
   const KernelKey k = key_of(h, red);
   const LaunchShape L = shape_of(h);
   const int v = h->cfg.variant;
@@ -771,12 +847,12 @@ static lbm_status one_step(lbm_t *h, bool red) {
       break;
     }
     case LBM_CG: {
-      lbm_status st = cg_step(h, red);
+      lbm_status st = cg_step(h, red, red_blocks);
       if (st != LBM_OK) return st;
       break;
     }
     case LBM_SWAP: {
-      lbm_status st = swap_step(h, red);
+      lbm_status st = swap_step(h, red, red_blocks);
       if (st != LBM_OK) return st;
       break;
     }
@@ -803,9 +879,10 @@ lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx) {
   if (!h->has_geometry) return fail(h, LBM_ERR_STATE, "no geometry");
   if (n < 1) return fail(h, LBM_ERR_INVALID_ARG, "step count must be >= 1");
   if (!is_natural(h)) return fail(h, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
-  lbm_status st = one_step(h, true);
+  int nred = 0;
+  lbm_status st = one_step(h, true, &nred);
   if (st != LBM_OK) return st;
-  launch_final_sum(h->d_partials, (int)shape_of(h).grid.x, h->d_out2, h->stream);
+  launch_final_sum(h->d_partials, nred, h->d_out2, h->stream);
   st = check_launch(h, "final_sum");
   if (st != LBM_OK) return st;
   for (int t = 1; t < n; ++t) {
@@ -816,7 +893,3 @@ lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx) {
 }
 
 }  // extern "C"
-
-// Compressed grid and swap are implemented in their own files.
-static lbm_status cg_step(lbm_t *h, bool) { return fail(h, LBM_ERR_UNSUPPORTED, "compressed grid not built"); }
-static lbm_status swap_step(lbm_t *h, bool) { return fail(h, LBM_ERR_UNSUPPORTED, "swap not built"); }

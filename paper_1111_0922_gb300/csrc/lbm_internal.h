@@ -50,6 +50,9 @@ inline void launch_step_kernel(int variant, int sub, const StepParams &p, const 
 
 // lbm_cg.cu: one slab of the compressed grid, and its periodic ghost planes
 void launch_cg_slab(const StepParams &p, const KernelKey &k, const LaunchShape &L);
+inline void launch_step_kernel_cg(const StepParams &p, const KernelKey &k, const LaunchShape &L) {
+  launch_cg_slab(p, k, L);
+}
 void launch_cg_ghost(const StepParams &p, int precision, int aos, int zo, cudaStream_t s);
 
 // lbm_swap.cu: one colour pass of the blocked swap
@@ -61,6 +64,8 @@ struct SwapTiles {
 };
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
 size_t swap_smem_bytes(const SwapTiles &t, int precision);
+int swap_colours(const SwapTiles &t, int px, int py, int pz);
+int swap_blocks(const SwapTiles &t, int px, int py, int pz, int colour);
 
 // lbm_setup.cu
 void launch_sphere_mask(uint8_t *solid, int nx, int ny, int nz, const int *periodic, int64_t nsph,

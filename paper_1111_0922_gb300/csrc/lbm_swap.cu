@@ -1,0 +1,175 @@
+// Swap algorithm (Sec. 5, Fig. 3, Tab. 4) on a full grid, push form, blocked.
+//
+// The serial swap collides a node into its reversed slots (the post-collision
+// PDF along c_i goes to the node's slot of the opposite direction) and then
+// completes each link to an already visited neighbour by exchanging the two
+// PDFs that travel along it; a link into a wall or solid needs no exchange.
+// That gives the natural next state for any visiting order in which a link is
+// exchanged after both of its nodes have collided.
+//
+// Here the order is blocked, as Sec. 5 allows: the box is cut into tiles, one
+// CTA per tile, and the tiles are coloured so that no two tiles sharing a link
+// have the same colour (per axis: tile index mod 2, a third colour for the
+// last tile of an odd periodic axis).  Colours run as consecutive launches.
+// Inside a CTA every node collides into shared memory; links inside the tile
+// are completed there; a link to a tile of an earlier colour is completed by
+// exchanging with global memory (that tile left its end reversed); a link to a
+// tile of a later colour is left reversed for that tile to complete.
+#include <algorithm>
+
+#include "lbm_dispatch.cuh"
+#include "lbm_internal.h"
+
+namespace lbmk {
+
+struct SwapPass {
+  int tx, ty, tz;              // tile extent
+  int ntx, nty, ntz;           // tiles per axis
+  int cx, cy, cz;              // colours per axis
+  int colour;                  // colour of this pass (cx-fastest)
+  int start[3], count[3];      // tiles of this colour per axis: start + 2k (or the odd tail tile)
+};
+
+__device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
+  if (nt == 1) return 0;
+  if (periodic && (nt & 1)) return t == nt - 1 ? 2 : (t & 1);
+  return t & 1;
+}
+
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+__global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
+  using T = typename C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);
+  Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
+  const Grid &g = p.g;
+  const int TN = sp.tx * sp.ty * sp.tz;
+  // which tile of this colour
+  const int b = blockIdx.x;
+  const int kx = b % sp.count[0], ky = (b / sp.count[0]) % sp.count[1], kz = b / (sp.count[0] * sp.count[1]);
+  const int tile[3] = {sp.start[0] + 2 * kx, sp.start[1] + 2 * ky, sp.start[2] + 2 * kz};
+  const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
+  const int t = threadIdx.x;
+  const int lx = t % sp.tx, ly = (t / sp.tx) % sp.ty, lz = t / (sp.tx * sp.ty);
+  const int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
+  const bool active = t < TN && x < g.nx && y < g.ny && z < g.nz && !grid_solid(g, x, y, z);
+  const int64_t s = active ? grid_slot(g, x, y, z) : 0;
+  double m = 0.0, jsum = 0.0;
+  if (active) {
+    T d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = L.ld(i, s);
+    T drho, rjx;
+    collide<T, FORCE>(d, T(p.omega), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+    m = 1.0 + (double)drho;
+    jsum = (double)rjx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) S[i * TN + t] = d[i];
+  }
+  __syncthreads();
+  if (active) {
+    L.st(0, s, S[t]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      // the PDF arriving along c_i comes from y = x - c_i
+      int a = x - CX(i), bb = y - CY(i), c = z - CZ(i);
+      const bool linked = wrap_axis(a, g.nx, g.px) && wrap_axis(bb, g.ny, g.py) && wrap_axis(c, g.nz, g.pz) &&
+                          !grid_solid(g, a, bb, c);
+      T v;
+      if (!linked) {
+        v = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
+      } else {
+        const int ta = a / sp.tx, tb = bb / sp.ty, tc = c / sp.tz;
+        if (ta == tile[0] && tb == tile[1] && tc == tile[2]) {
+          const int u = (a - org[0]) + sp.tx * ((bb - org[1]) + sp.ty * (c - org[2]));
+          v = S[i * TN + u];
+        } else {
+          const int col = axis_colour(ta, sp.ntx, g.px) +
+                          sp.cx * (axis_colour(tb, sp.nty, g.py) + sp.cy * axis_colour(tc, sp.ntz, g.pz));
+          if (col < sp.colour) {
+            // earlier tile: its reversed slot holds the PDF for us; give it ours
+            const int64_t ys = grid_slot(g, a, bb, c);
+            v = L.ld(OPP(i), ys);
+            L.st(OPP(i), ys, S[OPP(i) * TN + t]);
+          } else {
+            v = S[OPP(i) * TN + t];  // later tile completes the link
+          }
+        }
+      }
+      L.st(i, s, v);
+    }
+  }
+  if (RED) block_reduce_store(m, jsum, p.partials);
+}
+
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+struct LaunchSwap {
+  static void run(const StepParams &p, const SwapPass &sp, size_t smem, int blocks, cudaStream_t s) {
+    auto k = k_swap_pass<C, AOS, false, FORCE, RED>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, sp.tx * sp.ty * sp.tz, smem, s>>>(p, sp);
+  }
+};
+
+size_t swap_smem_bytes(const SwapTiles &t, int precision) {
+  return (size_t)Q * t.tx * t.ty * t.tz * (precision == 0 ? 8 : 4);
+}
+
+static void axis_set(int nt, int periodic, int colour, int &start, int &count) {
+  if (nt == 1) {
+    start = 0;
+    count = colour == 0 ? 1 : 0;
+    return;
+  }
+  if (periodic && (nt & 1)) {
+    if (colour == 2) {
+      start = nt - 1;
+      count = 1;
+    } else {
+      start = colour;
+      count = (nt - 1 - colour + 1) / 2;  // even tiles 0..nt-3 or odd 1..nt-2
+    }
+    return;
+  }
+  start = colour;
+  count = colour < nt ? (nt - colour + 1) / 2 : 0;
+}
+
+void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s) {
+  SwapPass sp;
+  sp.tx = t.tx;
+  sp.ty = t.ty;
+  sp.tz = t.tz;
+  sp.ntx = t.ntx;
+  sp.nty = t.nty;
+  sp.ntz = t.ntz;
+  auto ncol = [](int nt, int periodic) { return nt == 1 ? 1 : ((periodic && (nt & 1)) ? 3 : 2); };
+  sp.cx = ncol(t.ntx, p.g.px);
+  sp.cy = ncol(t.nty, p.g.py);
+  sp.cz = ncol(t.ntz, p.g.pz);
+  sp.colour = t.colour;
+  const int c0 = t.colour % sp.cx, c1 = (t.colour / sp.cx) % sp.cy, c2 = t.colour / (sp.cx * sp.cy);
+  axis_set(t.ntx, p.g.px, c0, sp.start[0], sp.count[0]);
+  axis_set(t.nty, p.g.py, c1, sp.start[1], sp.count[1]);
+  axis_set(t.ntz, p.g.pz, c2, sp.start[2], sp.count[2]);
+  const int blocks = sp.count[0] * sp.count[1] * sp.count[2];
+  if (blocks == 0) return;
+  dispatch<LaunchSwap>(k.precision, k.aos, false, k.force, k.red, p, sp, swap_smem_bytes(t, k.precision), blocks, s);
+}
+
+int swap_colours(const SwapTiles &t, int px, int py, int pz) {
+  auto ncol = [](int nt, int periodic) { return nt == 1 ? 1 : ((periodic && (nt & 1)) ? 3 : 2); };
+  return ncol(t.ntx, px) * ncol(t.nty, py) * ncol(t.ntz, pz);
+}
+
+int swap_blocks(const SwapTiles &t, int px, int py, int pz, int colour) {
+  auto ncol = [](int nt, int periodic) { return nt == 1 ? 1 : ((periodic && (nt & 1)) ? 3 : 2); };
+  const int cx = ncol(t.ntx, px), cy = ncol(t.nty, py);
+  int st, c0, c1, c2;
+  axis_set(t.ntx, px, colour % cx, st, c0);
+  axis_set(t.nty, py, (colour / cx) % cy, st, c1);
+  axis_set(t.ntz, pz, colour / (cx * cy), st, c2);
+  return c0 * c1 * c2;
+}
+
+}  // namespace lbmk
