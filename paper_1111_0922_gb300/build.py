@@ -54,24 +54,37 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every kernel file for sm_103a and link liblbm.so; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None,
+          objdir: str | None = None) -> str:
+    """Compile every kernel file for sm_103a and link liblbm.so (or `out`);
+    returns its path.  `extra`: additional nvcc flags (e.g. -D options)."""
+    global OBJ
+    target = out or OUT
+    if not force and out is None and up_to_date():
         return OUT
+    saved = OBJ
+    OBJ = objdir or OBJ
+    try:
+        return _build(target, extra, verbose)
+    finally:
+        OBJ = saved
+
+
+def _build(target, extra, verbose):
     os.makedirs(OBJ, exist_ok=True)
     srcs = sources()
     jobs = min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = OUT + ".tmp%d" % os.getpid()
+    tmp = target + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, OUT)
+    os.replace(tmp, target)
     if verbose:
-        print("built", OUT)
-    return OUT
+        print("built", target)
+    return target
 
 
 if __name__ == "__main__":

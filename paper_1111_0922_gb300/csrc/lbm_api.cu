@@ -173,17 +173,32 @@ static StepParams params_of(const lbm_t *h) {
   return p;
 }
 
+// Launch shape of the step kernels.  Full grid: 2D blocks over (x, y) (x
+// extent rounded up to a warp, capped at the block size), grid z over planes,
+// nodes_per_thread planes per thread.  Node list: 1D, nodes_per_thread nodes
+// per thread.
 static LaunchShape shape_of(const lbm_t *h) {
   LaunchShape L;
   const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 256;
   const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
-  int64_t blocks = (h->nn + (int64_t)bs * npt - 1) / ((int64_t)bs * npt);
-  if (blocks < 1) blocks = 1;
-  L.grid = dim3((unsigned)blocks);
-  L.block = dim3((unsigned)bs);
+  if (h->cfg.addressing == LBM_DIRECT) {
+    const int bx = (int)std::min<int64_t>(bs, round_up(h->cfg.nx, 32));
+    const int by = std::max(1, bs / bx);
+    const int64_t gx = (h->cfg.nx + bx - 1) / bx, gy = (h->cfg.ny + by - 1) / by;
+    const int64_t gz = std::min<int64_t>((h->cfg.nz + npt - 1) / npt, 65535);
+    L.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
+    L.block = dim3((unsigned)bx, (unsigned)by);
+  } else {
+    int64_t blocks = (h->nn + (int64_t)bs * npt - 1) / ((int64_t)bs * npt);
+    if (blocks < 1) blocks = 1;
+    L.grid = dim3((unsigned)blocks);
+    L.block = dim3((unsigned)bs);
+  }
   L.stream = h->stream;
   return L;
 }
+
+static int64_t blocks_of(const LaunchShape &L) { return (int64_t)L.grid.x * L.grid.y * L.grid.z; }
 
 static SwapTiles swap_tiles(const lbm_t *h) {
   SwapTiles t;
@@ -248,6 +263,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
     if (cfg->periodic[a] && n[a] < 2)
       return fail(nullptr, LBM_ERR_INVALID_ARG, "periodic axis %d needs extent >= 2", a);
   }
+  if (cfg->ny > 65535) return fail(nullptr, LBM_ERR_INVALID_ARG, "ny must be <= 65535");
   if ((int64_t)n[0] * n[1] * n[2] >= (int64_t)1 << 30)
     return fail(nullptr, LBM_ERR_INVALID_ARG, "box of %lld cells exceeds 2^30", (long long)n[0] * n[1] * n[2]);
   if (cfg->variant < LBM_TS || cfg->variant > LBM_ET) return fail(nullptr, LBM_ERR_INVALID_ARG, "variant");
@@ -436,7 +452,7 @@ static lbm_status build_geometry(lbm_t *h) {
   if (h->d_B) CUDA_TRY(h, cudaMemsetAsync(h->d_B, 0, h->state_bytes, h->stream));
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
-  int64_t need = std::max<int64_t>(L.grid.x, reduce_blocks_for(h->nn));
+  int64_t need = std::max<int64_t>(blocks_of(L), reduce_blocks_for(h->nn));
   if (c.variant == LBM_CG) need += (c.nz + h->cg_k - 2) / (h->cg_k - 1) + 1;  // one partial tile per slab
   if (c.variant == LBM_SWAP) {
     const SwapTiles t = swap_tiles(h);
@@ -815,7 +831,7 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
 }
 
 static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
-  if (red_blocks) *red_blocks = (int)shape_of(h).grid.x;
+  if (red_blocks) *red_blocks = (int)blocks_of(shape_of(h));
   const KernelKey k = key_of(h, red);
   const LaunchShape L = shape_of(h);
   const int v = h->cfg.variant;

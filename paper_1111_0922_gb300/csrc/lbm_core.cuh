@@ -226,23 +226,95 @@ struct StepParams {
   int zo_read, zo_write;  // compressed grid: plane offsets of the old and new state
 };
 
-// Per-thread node context for full-grid addressing.
+// Hide a value's provenance from the optimiser: addresses derived from the
+// result are recomputed instead of kept live from an earlier phase (loads and
+// stores of a node touch the same slots, and holding 19 64-bit addresses
+// across the collision costs ~40 registers).
+__device__ __forceinline__ int launder(int v) {
+  asm volatile("" : "+r"(v));
+  return v;
+}
+
+// Per-thread node context for full-grid addressing.  The wrap-adjusted cell
+// deltas to the -1/+1 neighbour along each axis are computed once per node
+// (on a wall face the delta points into the halo and a wall bit is set), so
+// a neighbour slot costs a few 32-bit adds.  Step kernels map threads to
+// cells with a 2D block over (x, y) and grid z over planes; the state
+// kernels use a flat cell index.
 struct DirectNode {
   int x, y, z;
-  int s;
+  int s;      // own storage slot
+  int cell;   // own cell (solid mask index)
+  int dx[2], dy[2], dz[2];
+  unsigned wall;  // bit 2a + side: face (axis a, -1 / +1 side) is a wall
+
+  __device__ __forceinline__ bool setup(const Grid &g) {
+    if (grid_solid(g, x, y, z)) return false;
+    s = (int)grid_slot(g, x, y, z);
+    cell = x + g.nx * (y + g.ny * z);
+    wall = 0;
+    dx[0] = -1;
+    dx[1] = 1;
+    dy[0] = -1;
+    dy[1] = 1;
+    dz[0] = -1;
+    dz[1] = 1;
+    if (x == 0) { if (g.px) dx[0] = g.nx - 1; else wall |= 1u; }
+    if (x == g.nx - 1) { if (g.px) dx[1] = 1 - g.nx; else wall |= 2u; }
+    if (y == 0) { if (g.py) dy[0] = g.ny - 1; else wall |= 4u; }
+    if (y == g.ny - 1) { if (g.py) dy[1] = 1 - g.ny; else wall |= 8u; }
+    if (z == 0) { if (g.pz) dz[0] = g.nz - 1; else wall |= 16u; }
+    if (z == g.nz - 1) { if (g.pz) dz[1] = 1 - g.nz; else wall |= 32u; }
+    return true;
+  }
+  // flat cell index (state kernels)
   __device__ __forceinline__ bool init(const StepParams &p, int64_t n) {
     const Grid &g = p.g;
     x = (int)(n % g.nx);
-    int64_t r = n / g.nx;
+    const int64_t r = n / g.nx;
     y = (int)(r % g.ny);
     z = (int)(r / g.ny);
-    if (grid_solid(g, x, y, z)) return false;
-    s = (int)grid_slot(g, x, y, z);
-    return true;
+    return setup(g);
   }
-  // slot of the fluid neighbour along c_i, or -1
+  // step kernels: x, y from the 2D block, z = it
+  __device__ static __forceinline__ int64_t it_begin(const StepParams &) { return blockIdx.z; }
+  __device__ static __forceinline__ int64_t it_end(const StepParams &p) { return p.g.nz; }
+  __device__ static __forceinline__ int64_t it_step(const StepParams &) { return gridDim.z; }
+  __device__ __forceinline__ bool init_it(const StepParams &p, int64_t it) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
+    z = (int)it;
+    if (x >= p.g.nx || y >= p.g.ny) return false;
+    return setup(p.g);
+  }
+  __device__ __forceinline__ void launder_all() {
+    s = launder(s);
+    cell = launder(cell);
+    dx[0] = launder(dx[0]);
+    dx[1] = launder(dx[1]);
+    dy[0] = launder(dy[0]);
+    dy[1] = launder(dy[1]);
+    dz[0] = launder(dz[0]);
+    dz[1] = launder(dz[1]);
+    wall = (unsigned)launder((int)wall);
+  }
+  // storage slot of x + c_i whether fluid or not (the halo beyond a wall)
+  __device__ __forceinline__ int pos(const StepParams &p, int i) const {
+    const int ex = CX(i) < 0 ? dx[0] : (CX(i) > 0 ? dx[1] : 0);
+    const int ey = CY(i) < 0 ? dy[0] : (CY(i) > 0 ? dy[1] : 0);
+    const int ez = CZ(i) < 0 ? dz[0] : (CZ(i) > 0 ? dz[1] : 0);
+    return s + ex + (int)p.g.sx * ey + (int)p.g.sxy * ez;
+  }
+  // slot of the fluid neighbour along c_i, or -1 for a wall or solid link
   __device__ __forceinline__ int nb(const StepParams &p, int i) const {
-    return (int)grid_neighbour(p.g, x, y, z, CX(i), CY(i), CZ(i));
+    const unsigned need = (CX(i) < 0 ? 1u : 0u) | (CX(i) > 0 ? 2u : 0u) | (CY(i) < 0 ? 4u : 0u) |
+                          (CY(i) > 0 ? 8u : 0u) | (CZ(i) < 0 ? 16u : 0u) | (CZ(i) > 0 ? 32u : 0u);
+    if (wall & need) return -1;
+    const int ex = CX(i) < 0 ? dx[0] : (CX(i) > 0 ? dx[1] : 0);
+    const int ey = CY(i) < 0 ? dy[0] : (CY(i) > 0 ? dy[1] : 0);
+    const int ez = CZ(i) < 0 ? dz[0] : (CZ(i) > 0 ? dz[1] : 0);
+    if (p.g.solid && p.g.solid[cell + ex + p.g.nx * (ey + p.g.ny * ez)]) return -1;
+    return s + ex + (int)p.g.sx * ey + (int)p.g.sxy * ez;
   }
 };
 
@@ -253,6 +325,13 @@ struct IndirectNode {
     s = (int)n;
     return true;
   }
+  __device__ static __forceinline__ int64_t it_begin(const StepParams &) {
+    return (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  }
+  __device__ static __forceinline__ int64_t it_end(const StepParams &p) { return p.nnodes; }
+  __device__ static __forceinline__ int64_t it_step(const StepParams &) { return (int64_t)gridDim.x * blockDim.x; }
+  __device__ __forceinline__ bool init_it(const StepParams &p, int64_t it) { return init(p, it); }
+  __device__ __forceinline__ void launder_all() { s = launder(s); }
   __device__ __forceinline__ int nb(const StepParams &p, int i) const {
     return __ldg(p.idx + (int64_t)(i - 1) * p.ipad + s);
   }
@@ -260,6 +339,7 @@ struct IndirectNode {
 
 // ---------------------------------------------------------------------------
 // Block reduction of (mass, flux) into per-block FP64 partials.
+// Works for 1D, 2D and 3D blocks and grids (block id in launch order).
 __device__ __forceinline__ void block_reduce_store(double m, double j, double *partials) {
   __shared__ double sm[32], sj[32];
 #pragma unroll
@@ -267,14 +347,15 @@ __device__ __forceinline__ void block_reduce_store(double m, double j, double *p
     m += __shfl_xor_sync(0xffffffffu, m, o);
     j += __shfl_xor_sync(0xffffffffu, j, o);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
   if (lane == 0) {
     sm[warp] = m;
     sj[warp] = j;
   }
   __syncthreads();
   if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
     m = lane < nw ? sm[lane] : 0.0;
     j = lane < nw ? sj[lane] : 0.0;
 #pragma unroll
@@ -283,8 +364,9 @@ __device__ __forceinline__ void block_reduce_store(double m, double j, double *p
       j += __shfl_xor_sync(0xffffffffu, j, o);
     }
     if (lane == 0) {
-      partials[2 * blockIdx.x] = m;
-      partials[2 * blockIdx.x + 1] = j;
+      const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+      partials[2 * b] = m;
+      partials[2 * b + 1] = j;
     }
   }
 }

@@ -22,6 +22,20 @@ __device__ __forceinline__ Lattice<C, AOS> lattice_of(void *p, const StepParams 
   return L;
 }
 
+// Launch bounds of the step kernels: at most LBM_STEP_MAXT threads per block
+// and at least LBM_STEP_MINB resident blocks per SM (a register budget).
+#ifndef LBM_STEP_MAXT
+#define LBM_STEP_MAXT 512
+#endif
+#ifdef LBM_STEP_MINB
+#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT, LBM_STEP_MINB)
+#else
+#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT)
+#endif
+
+template <bool IND>
+using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
+
 template <typename T, bool FORCE>
 __device__ __forceinline__ void run_collision(T (&d)[Q], const StepParams &p, double &m, double &j) {
   T drho, rjx;
@@ -30,24 +44,26 @@ __device__ __forceinline__ void run_collision(T (&d)[Q], const StepParams &p, do
   j += (double)rjx;
 }
 
-#define LBM_GRID_LOOP(n) \
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.nnodes; n += (int64_t)gridDim.x * blockDim.x)
+// Iterate this thread's nodes: a flat grid-stride loop over the node list
+// (IDX addressing), or the planes of this thread's (x, y) column (full grid).
+#define LBM_NODE_LOOP(Node, it) for (int64_t it = Node::it_begin(p); it < Node::it_end(p); it += Node::it_step(p))
 
 // ---------------------------------------------------------------------------
 // Two-step, kernel 1 (Tab. 1, collision): A -> B at the same slot.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_ts_collide(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_ts_collide(StepParams p) {
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
     T d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
     run_collision<T, FORCE>(d, p, m, j);
+    nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
   }
@@ -57,12 +73,12 @@ __global__ void __launch_bounds__(512) k_ts_collide(StepParams p) {
 // Two-step, kernel 2 (Tab. 1, propagation), pull form: A_i(x) = B_i(x - c_i),
 // or B_opp(i)(x) across a solid/wall link.  Raw copies: bit-exact.
 template <class C, int AOS, class Node>
-__global__ void __launch_bounds__(512) k_ts_stream(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
     *A.at(0, nd.s) = *B.at(0, nd.s);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -74,18 +90,19 @@ __global__ void __launch_bounds__(512) k_ts_stream(StepParams p) {
 
 // One-step push (Fig. 1a,b): read A at the node, write B at the neighbours.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_os_push(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_os_push(StepParams p) {
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
     T d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
     run_collision<T, FORCE>(d, p, m, j);
+    nd.launder_all();
     B.st(0, nd.s, d[0]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -102,14 +119,14 @@ __global__ void __launch_bounds__(512) k_os_push(StepParams p) {
 // One-step pull (Fig. 1c,d): gather from the neighbours in A, write B at the
 // node.  The stored state is post-collision.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_os_pull(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_os_pull(StepParams p) {
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
     T d[Q];
     d[0] = A.ld(0, nd.s);
 #pragma unroll
@@ -118,6 +135,7 @@ __global__ void __launch_bounds__(512) k_os_pull(StepParams p) {
       d[i] = src >= 0 ? A.ld(i, src) : A.ld(OPP(i), nd.s);
     }
     run_collision<T, FORCE>(d, p, m, j);
+    nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
   }
@@ -127,17 +145,18 @@ __global__ void __launch_bounds__(512) k_os_pull(StepParams p) {
 // AA pattern, even step (Fig. 5a,b): node-local; the post-collision PDF of
 // direction i goes to the node's slot of the opposite direction.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_aa_even(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_aa_even(StepParams p) {
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
     T d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
     run_collision<T, FORCE>(d, p, m, j);
+    nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) A.st(OPP(i), nd.s, d[i]);
   }
@@ -149,28 +168,34 @@ __global__ void __launch_bounds__(512) k_aa_even(StepParams p) {
 // of x + c_i (own opposite slot across a solid link).  Every slot written was
 // read by the same thread.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_aa_odd(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
+  LBM_NODE_LOOP(Node, it) {
     Node nd;
-    if (!nd.init(p, n)) continue;
+    if (!nd.init_it(p, it)) continue;
+    // IDX entries are loaded once and kept; full-grid neighbours are cheap to
+    // recompute after the collision
+    constexpr bool kHold = std::is_same<Node, IndirectNode>::value;
     int nb[Q];
+    if (kHold) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) nb[i] = nd.nb(p, i);
+      for (int i = 1; i < Q; ++i) nb[i] = nd.nb(p, i);
+    }
     T d[Q];
     d[0] = A.ld(0, nd.s);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int src = nb[OPP(i)];
+      const int src = kHold ? nb[OPP(i)] : nd.nb(p, OPP(i));
       d[i] = src >= 0 ? A.ld(OPP(i), src) : A.ld(i, nd.s);
     }
     run_collision<T, FORCE>(d, p, m, j);
+    nd.launder_all();
     A.st(0, nd.s, d[0]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int dst = nb[i];
+      const int dst = kHold ? nb[i] : nd.nb(p, i);
       if (dst >= 0)
         A.st(i, dst, d[i]);
       else
@@ -179,6 +204,12 @@ __global__ void __launch_bounds__(512) k_aa_odd(StepParams p) {
   }
   if (RED) block_reduce_store(m, j, p.partials);
 }
+
+// Esoteric-twist helpers on a full grid (unused for node lists).
+__device__ __forceinline__ int et_pos(const DirectNode &nd, const StepParams &p, int i) { return nd.pos(p, i); }
+__device__ __forceinline__ int et_pos(const IndirectNode &nd, const StepParams &, int) { return nd.s; }
+__device__ __forceinline__ bool et_linked(const DirectNode &nd, const StepParams &p, int i) { return nd.nb(p, i) >= 0; }
+__device__ __forceinline__ bool et_linked(const IndirectNode &, const StepParams &, int) { return true; }
 
 // Esoteric twist (Fig. 6): PDF f_i of node x lives in array map[i] at x for
 // the rest and odd directions, and at x + c_{i-1} for even i (the neighbour
@@ -191,50 +222,52 @@ __global__ void __launch_bounds__(512) k_aa_odd(StepParams p) {
 //             slot of x + c_{2k+1} in bits 0..30 (a ghost slot >= nfluid when
 //             that cell is solid) and in bit 31 whether x + c_{2k+2} is solid.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_et(StepParams p) {
+__global__ void LBM_STEP_BOUNDS k_et(StepParams p) {
   using T = typename C::T;
+  using Node = NodeOf<IND>;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
-  LBM_GRID_LOOP(n) {
-    int s;
-    int pos[10];
-    bool lp[10], lm[10];
+  LBM_NODE_LOOP(Node, it) {
+    Node nd;
+    if (!nd.init_it(p, it)) continue;
+    uint32_t w[10];  // packed index words (IDX addressing), kept across the collision
     if (IND) {
-      s = (int)n;
 #pragma unroll
-      for (int k = 1; k <= 9; ++k) {
-        const uint32_t w = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.ipad + n);
-        pos[k] = (int)(w & 0x7fffffffu);
-        lp[k] = pos[k] < p.nfluid;
-        lm[k] = (w >> 31) == 0u;
-      }
-    } else {
-      DirectNode nd;
-      if (!nd.init(p, n)) continue;
-      s = nd.s;
-#pragma unroll
-      for (int k = 1; k <= 9; ++k) {
-        const int i = 2 * k - 1;
-        pos[k] = (int)grid_position(p.g, nd.x, nd.y, nd.z, CX(i), CY(i), CZ(i));
-        lp[k] = nd.nb(p, i) >= 0;
-        lm[k] = nd.nb(p, i + 1) >= 0;
-      }
+      for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.ipad + nd.s);
     }
     T d[Q];
-    d[0] = A.ld(p.map[0], s);
+    d[0] = A.ld(p.map[0], nd.s);
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
-      d[2 * k - 1] = A.ld(p.map[2 * k - 1], s);
-      d[2 * k] = A.ld(p.map[2 * k], pos[k]);
+      const int i = 2 * k - 1;
+      d[i] = A.ld(p.map[i], nd.s);
+      const int pos = IND ? (int)(w[k] & 0x7fffffffu) : et_pos(nd, p, i);
+      d[i + 1] = A.ld(p.map[i + 1], pos);
     }
     run_collision<T, FORCE>(d, p, m, j);
-    A.st(p.map[0], s, d[0]);
+    nd.launder_all();
+    if (IND) {
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)launder((int)w[k]);
+    }
+    A.st(p.map[0], nd.s, d[0]);
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
-      // odd direction 2k-1: to x + c_{2k-1}
-      A.st(lp[k] ? p.map[2 * k] : p.map[2 * k - 1], pos[k], d[2 * k - 1]);
-      // even direction 2k: to x itself
-      A.st(lm[k] ? p.map[2 * k - 1] : p.map[2 * k], s, d[2 * k]);
+      const int i = 2 * k - 1;
+      int pos;
+      bool lp, lm;
+      if (IND) {
+        pos = (int)(w[k] & 0x7fffffffu);
+        lp = pos < p.nfluid;
+        lm = (w[k] >> 31) == 0u;
+      } else {
+        pos = et_pos(nd, p, i);
+        lp = et_linked(nd, p, i);
+        lm = et_linked(nd, p, i + 1);
+      }
+      // odd direction i: to x + c_i; even direction i+1: to x itself
+      A.st(lp ? p.map[i + 1] : p.map[i], pos, d[i]);
+      A.st(lm ? p.map[i] : p.map[i + 1], nd.s, d[i + 1]);
     }
   }
   if (RED) block_reduce_store(m, j, p.partials);
@@ -242,8 +275,6 @@ __global__ void __launch_bounds__(512) k_et(StepParams p) {
 
 // ---------------------------------------------------------------------------
 // Launchers.
-template <bool IND>
-using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
 
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchTS {

@@ -45,12 +45,11 @@ __global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
   const Grid &g = p.g;
   const int TN = sp.tx * sp.ty * sp.tz;
   // which tile of this colour
-  const int b = blockIdx.x;
-  const int kx = b % sp.count[0], ky = (b / sp.count[0]) % sp.count[1], kz = b / (sp.count[0] * sp.count[1]);
+  const int kx = blockIdx.x, ky = blockIdx.y, kz = blockIdx.z;
   const int tile[3] = {sp.start[0] + 2 * kx, sp.start[1] + 2 * ky, sp.start[2] + 2 * kz};
   const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
-  const int t = threadIdx.x;
-  const int lx = t % sp.tx, ly = (t / sp.tx) % sp.ty, lz = t / (sp.tx * sp.ty);
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
   const int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
   const bool active = t < TN && x < g.nx && y < g.ny && z < g.nz && !grid_solid(g, x, y, z);
   const int64_t s = active ? grid_slot(g, x, y, z) : 0;
@@ -79,13 +78,31 @@ __global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
       if (!linked) {
         v = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
       } else {
-        const int ta = a / sp.tx, tb = bb / sp.ty, tc = c / sp.tz;
-        if (ta == tile[0] && tb == tile[1] && tc == tile[2]) {
+        // tile of the source cell along each axis, by comparison with this
+        // tile's bounds (no division): same, previous or next (wrapping)
+        const int src[3] = {a, bb, c};
+        const int d[3] = {-CX(i), -CY(i), -CZ(i)};
+        const int ext[3] = {sp.tx, sp.ty, sp.tz};
+        const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
+        const int per[3] = {g.px, g.py, g.pz};
+        int nt_idx[3];
+        bool same = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          if (src[ax] >= org[ax] && src[ax] < org[ax] + ext[ax]) {
+            nt_idx[ax] = tile[ax];
+          } else {
+            same = false;
+            nt_idx[ax] = d[ax] < 0 ? (tile[ax] == 0 ? nt[ax] - 1 : tile[ax] - 1)
+                                   : (tile[ax] == nt[ax] - 1 ? 0 : tile[ax] + 1);
+          }
+        }
+        if (same) {
           const int u = (a - org[0]) + sp.tx * ((bb - org[1]) + sp.ty * (c - org[2]));
           v = S[i * TN + u];
         } else {
-          const int col = axis_colour(ta, sp.ntx, g.px) +
-                          sp.cx * (axis_colour(tb, sp.nty, g.py) + sp.cy * axis_colour(tc, sp.ntz, g.pz));
+          const int col = axis_colour(nt_idx[0], nt[0], per[0]) +
+                          sp.cx * (axis_colour(nt_idx[1], nt[1], per[1]) + sp.cy * axis_colour(nt_idx[2], nt[2], per[2]));
           if (col < sp.colour) {
             // earlier tile: its reversed slot holds the PDF for us; give it ours
             const int64_t ys = grid_slot(g, a, bb, c);
@@ -104,10 +121,10 @@ __global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
 
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchSwap {
-  static void run(const StepParams &p, const SwapPass &sp, size_t smem, int blocks, cudaStream_t s) {
+  static void run(const StepParams &p, const SwapPass &sp, size_t smem, dim3 blocks, cudaStream_t s) {
     auto k = k_swap_pass<C, AOS, false, FORCE, RED>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<blocks, sp.tx * sp.ty * sp.tz, smem, s>>>(p, sp);
+    k<<<blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp);
   }
 };
 
@@ -152,8 +169,8 @@ void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &
   axis_set(t.ntx, p.g.px, c0, sp.start[0], sp.count[0]);
   axis_set(t.nty, p.g.py, c1, sp.start[1], sp.count[1]);
   axis_set(t.ntz, p.g.pz, c2, sp.start[2], sp.count[2]);
-  const int blocks = sp.count[0] * sp.count[1] * sp.count[2];
-  if (blocks == 0) return;
+  if (sp.count[0] * sp.count[1] * sp.count[2] == 0) return;
+  const dim3 blocks(sp.count[0], sp.count[1], sp.count[2]);
   dispatch<LaunchSwap>(k.precision, k.aos, false, k.force, k.red, p, sp, swap_smem_bytes(t, k.precision), blocks, s);
 }
 
