@@ -186,6 +186,43 @@ lbm_status lbm_macroscopics(lbm_t *h, double *rho, double *u, int on_device);
 /* Wait for the handle's stream and report device-side errors. */
 lbm_status lbm_sync(lbm_t *h);
 
+/* Mass and flux of a caller-owned natural PDF array, with no allocation.
+ * (This entry point has no counterpart in the paper.)
+ *
+ * For callers that cannot allocate device memory: a serving loop or a host
+ * application whose device memory is already handed to its own pool (such
+ * as PyTorch's caching allocator) cannot get more without a device-wide
+ * synchronisation or a failure, and a latency-bound loop cannot afford the
+ * implicit synchronisation of cudaFree.  This call makes no cudaMalloc,
+ * cudaFree or other allocating call; its only scratch, the per-block partial
+ * sums, is a fixed array inside the library (LBM_NOALLOC_MAX_BLOCKS x 2
+ * doubles = 256 KiB on every GPU that loads the library, kept until exit).
+ *
+ *   f_dev      device array of the deviations f_i - w_i of n nodes in the
+ *              library's storage form: precision LBM_F64 / LBM_F32 (values
+ *              as is) or LBM_F16S (FP16 holding (f_i - w_i) * f16_scale);
+ *              layout LBM_SOA (direction i of node k at i * npad + k,
+ *              npad >= n) or LBM_AOS (at k * 19 + i, npad ignored)
+ *   gx         body acceleration along x (the flux is sum rho u_x with
+ *              u = (sum c f + rho g / 2) / rho, as lbm_flux)
+ *   out_dev    device pointer to 2 doubles: sum rho, sum rho u_x (FP64,
+ *              fixed summation order: node chunks of LBM_NOALLOC_CHUNK)
+ *   stream     cudaStream_t to enqueue on (NULL = default stream)
+ *
+ * Limits and errors: n must be in [1, LBM_NOALLOC_MAX_BLOCKS *
+ * LBM_NOALLOC_CHUNK] (2^30 nodes), else LBM_ERR_INVALID_ARG; bad pointers or
+ * enums give LBM_ERR_INVALID_ARG; a launch failure gives LBM_ERR_CUDA.
+ * The first call on a device looks up the scratch's device address (a
+ * one-time set-up per device, done with that device current); make that first
+ * call before any stream capture.  All calls share the one scratch array and
+ * each rewrites the partials it reads: calls that may overlap on the GPU
+ * (other streams or threads) race on it and must be ordered by the caller.
+ * Asynchronous: the result is in out_dev once the stream reaches it. */
+#define LBM_NOALLOC_MAX_BLOCKS 16384
+#define LBM_NOALLOC_CHUNK 65536
+lbm_status lbm_flux_noalloc(const void *f_dev, int32_t precision, int32_t layout, int64_t n, int64_t npad,
+                            double f16_scale, double gx, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,8 @@ SIGNATURES = {
     "lbm_flux": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "lbm_macroscopics": (_I, [_P, _P, _P, _I]),
     "lbm_sync": (_I, [_P]),
+    "lbm_flux_noalloc": (_I, [_P, ctypes.c_int32, ctypes.c_int32, _I64, _I64, ctypes.c_double,
+                              ctypes.c_double, _P, _P]),
 }
 
 _lib = None
@@ -236,6 +238,20 @@ def lbm_macroscopics(h, n=None, rho=None, u=None, on_device=False, want_rho=True
 
 def lbm_sync(h):
     _check(h, load().lbm_sync(h))
+
+
+def lbm_flux_noalloc(f_dev, precision, layout, n, npad, f16_scale, gx, out_dev, stream=None):
+    """Mass and flux of a caller-owned natural PDF array into out_dev (2
+    doubles on the device), for callers that cannot allocate device memory:
+    the library allocates nothing for this call (its scratch is a fixed
+    256 KiB array inside the library).  Calls that overlap on the GPU share
+    that scratch and must be ordered by the caller; the first call on a
+    device does a one-time set-up and should come before any stream capture."""
+    st = load().lbm_flux_noalloc(_ptr(f_dev), int(precision), int(layout), int(n), int(npad),
+                                 float(f16_scale), float(gx), _ptr(out_dev),
+                                 ctypes.c_void_p(int(stream) if stream else 0))
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_flux_noalloc rejected the call")
 
 
 # ---------------------------------------------------------------------------
