@@ -293,6 +293,40 @@ def run_sweep(torch, lbm, args, hbm):
     return out
 
 
+def run_sparse(torch, lbm, args, hbm):
+    """512^3 periodic sphere pack (r = 8, porosity 0.6, seed 3; g = 1e-6 x,
+    omega 1): AA pattern and esoteric twist on the IDX node list, FP32 and FP16
+    storage, SoA."""
+    dims = (512, 512, 512)
+    pack = inputs.sphere_pack(dims, 0.6, radius=8.0, seed=SEED + 1)
+    out = {"workload": "periodic 512^3 sphere pack, r = 8, porosity 0.6 (seed 3), "
+                       "%d spheres, g = 1e-6 x, omega 1.0, from rest" % pack.nspheres}
+    for variant in ("aa", "et"):
+        for precision in ("f32", "f16s"):
+            key = "%s/%s/indirect" % (variant, precision)
+            lat = lbm.Lattice(dims, (1, 1, 1), variant=variant, addressing="indirect", precision=precision,
+                              omega=1.0, force=(1e-6, 0.0, 0.0))
+            t0 = time.perf_counter()
+            lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
+            lat.init()
+            torch.cuda.synchronize()
+            t_geo = time.perf_counter() - t0
+            lat.step(4)
+            total, _ = timed_steps(torch, lat, args.sparse_steps, per_launch=False)
+            info = lat.info
+            n = int(info.nodes)
+            mflups = n * args.sparse_steps / total / 1e6
+            roof = model.roof_mflups(variant, True, precision, hbm)
+            out[key] = {"mflups": round(mflups, 1), "roof_mflups": round(roof, 1), "frac": round(mflups / roof, 4),
+                        "bytes_per_flup": model.gpu_bytes(variant, True, precision), "fluid_nodes": n,
+                        "porosity": round(n / info.cells, 4), "ghost_slots": int(info.storage_nodes - n),
+                        "setup_s": round(t_geo, 2)}
+            lat.close()
+            torch.cuda.empty_cache()
+            log("sparse", key, out[key])
+    return out
+
+
 def main_gb300(args):
     import torch
 
@@ -338,6 +372,8 @@ def main_gb300(args):
         result["cpu_baseline"] = run_cpu_baseline(args.cpu_seconds)
     if rank == 0 and not args.no_sweep:
         result["variants"] = run_sweep(torch, lbm, args, hbm)
+    if rank == 0 and not args.no_sparse:
+        result["sparse"] = run_sparse(torch, lbm, args, hbm)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -394,6 +430,8 @@ def parse(argv=None):
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--sparse-steps", type=int, default=50)
     a = ap.parse_args(argv)
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")

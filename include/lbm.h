@@ -91,7 +91,7 @@ typedef struct lbm_config {
   double omega;              /* BGK relaxation rate, 0 < omega < 2 (0 = identity collision) */
   double force[3];           /* body acceleration g (Guo forcing) */
   double f16_scale;          /* LBM_F16S: scale S (power of two); 0 = choose from force */
-  int32_t block_size;        /* threads per block (multiple of 32, <= 1024); 0 = default 256 */
+  int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128 */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default */
   int32_t cg_shift;          /* LBM_CG: shift k in planes (direct) >= 2; 0 = default */
   int32_t reserved;

@@ -179,7 +179,7 @@ static StepParams params_of(const lbm_t *h) {
 // per thread.
 static LaunchShape shape_of(const lbm_t *h) {
   LaunchShape L;
-  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 256;
+  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
   const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
   if (h->cfg.addressing == LBM_DIRECT) {
     const int bx = (int)std::min<int64_t>(bs, round_up(h->cfg.nx, 32));
@@ -274,8 +274,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (!(cfg->omega >= 0.0 && cfg->omega < 2.0)) return fail(nullptr, LBM_ERR_INVALID_ARG, "omega must be in [0, 2)");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->force[a])) return fail(nullptr, LBM_ERR_INVALID_ARG, "force");
-  if (cfg->block_size != 0 && (cfg->block_size % 32 != 0 || cfg->block_size < 32 || cfg->block_size > 512))
-    return fail(nullptr, LBM_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 512]");
+  if (cfg->block_size != 0 && (cfg->block_size % 32 != 0 || cfg->block_size < 32 || cfg->block_size > 256))
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 256]");
   if (cfg->nodes_per_thread < 0 || cfg->nodes_per_thread > 16)
     return fail(nullptr, LBM_ERR_INVALID_ARG, "nodes_per_thread must be in [0, 16]");
   if (cfg->f16_scale < 0.0 || !std::isfinite(cfg->f16_scale))

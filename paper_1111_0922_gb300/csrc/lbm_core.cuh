@@ -37,21 +37,26 @@ __host__ __device__ constexpr double WD(int i) {
 // Storage codecs.  Every precision stores the deviation d_i = f_i - w_i
 // (rho0 = 1).  F16S stores round(d_i * S) with a power-of-two S, so decoding
 // is exact and only the final rounding to FP16 loses precision.
+// kMinBlocks: resident 256-thread blocks per SM the step kernels are built
+// for (a register budget: 2 -> 128, 3 -> 85 registers per thread).
 struct CodecF64 {
   using S = double;  // stored
   using T = double;  // computed
+  static constexpr int kMinBlocks = 2;
   __device__ static __forceinline__ T dec(S v, float) { return v; }
   __device__ static __forceinline__ S enc(T v, float) { return v; }
 };
 struct CodecF32 {
   using S = float;
   using T = float;
+  static constexpr int kMinBlocks = 3;
   __device__ static __forceinline__ T dec(S v, float) { return v; }
   __device__ static __forceinline__ S enc(T v, float) { return v; }
 };
 struct CodecF16S {
   using S = __half;
   using T = float;
+  static constexpr int kMinBlocks = 3;
   __device__ static __forceinline__ T dec(S v, float inv_scale) { return __half2float(v) * inv_scale; }
   __device__ static __forceinline__ S enc(T v, float scale) { return __float2half_rn(v * scale); }
 };

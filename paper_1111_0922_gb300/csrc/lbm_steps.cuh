@@ -23,15 +23,12 @@ __device__ __forceinline__ Lattice<C, AOS> lattice_of(void *p, const StepParams 
 }
 
 // Launch bounds of the step kernels: at most LBM_STEP_MAXT threads per block
-// and at least LBM_STEP_MINB resident blocks per SM (a register budget).
+// and at least C::kMinBlocks resident blocks per SM (the register budget
+// that keeps enough loads in flight to cover HBM latency).
 #ifndef LBM_STEP_MAXT
-#define LBM_STEP_MAXT 512
+#define LBM_STEP_MAXT 256
 #endif
-#ifdef LBM_STEP_MINB
-#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT, LBM_STEP_MINB)
-#else
-#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT)
-#endif
+#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks)
 
 template <bool IND>
 using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
