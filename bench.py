@@ -143,6 +143,21 @@ def gpu_smi_id(torch, dev):
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(torch, value: float, device) -> float:
+    """Largest value over all ranks (the job time of N replicas)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(nodes_per_rank: int, steps: int, world: int, t_max: float) -> float:
+    """Whole-job MFLUP/s of `world` replicas that each updated nodes_per_rank
+    nodes `steps` times, the slowest taking t_max seconds."""
+    return world * nodes_per_rank * steps / t_max / 1e6
+
+
 def make_lattice(lbm, variant, precision, layout, addressing="direct", dims=DIMS, omega=OMEGA,
                  force=(0.0, 0.0, 0.0), **kw):
     return lbm.Lattice(dims, (1, 1, 1), variant=variant, addressing=addressing, layout=layout,
@@ -192,11 +207,7 @@ def run_headline(torch, lbm, args, rank, world):
         torch.distributed.barrier()
     clocks = sampler.stop()
     info = lat.info
-    t_max = total
-    if world > 1:
-        t = torch.tensor([total], device=f"cuda:{dev}", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(torch, total, f"cuda:{dev}")
     kernels = args.steps * info.kernels_per_step
     lat.close()
     del rho_dev
@@ -327,6 +338,103 @@ def run_sparse(torch, lbm, args, hbm):
     return out
 
 
+def run_batch(torch, lbm, args):
+    """64 sphere packs, cube sides U{32..192}, porosity U[0.3, 0.8), r = 8
+    (seed 4); FP32 AA pattern on concatenated node lists, launch shape from the
+    autotuner; every geometry advanced in rounds of 100 steps until its flux
+    changes by less than 1e-6 (relative) between rounds, then retired."""
+    from paper_1111_0922_gb300 import permeability
+
+    items = inputs.batch_packs(args.batch_count, seed=4)
+    est = sum(int(it.side ** 3 * it.porosity) for it in items)
+    cap = int(est * 1.15) + 4096 * (len(items) + 1)
+    b = lbm.Batch(cap, variant="aa", precision="f32", max_geometries=len(items) + 1)
+    t0 = time.perf_counter()
+    slots = {}
+    for i, it in enumerate(items):
+        slots[b.admit(it.pack, 1.0, (1e-6, 0.0, 0.0))] = i
+    torch.cuda.synchronize()
+    t_admit = time.perf_counter() - t0
+    nodes_total = b.info.active_nodes
+    bs, npt, tuned = b.tune(rounds=1, k=10)
+    # restart every geometry from rest after tuning: release and re-admit
+    for slot in list(slots):
+        b.release(slot)
+    slots = {b.admit(items[i].pack, 1.0, (1e-6, 0.0, 0.0)): i for i in range(len(items))}
+    prev = {}
+    done = {}
+    updates = 0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    while slots and time.perf_counter() - t1 < args.batch_seconds:
+        active_nodes = b.info.active_nodes
+        b.round(100)
+        updates += 100 * active_nodes
+        for slot in list(slots):
+            _, flux, steps = b.poll(slot)
+            if slot in prev and abs(flux - prev[slot]) < 1e-6 * abs(flux):
+                it = items[slots[slot]]
+                done[slots[slot]] = (permeability.permeability(flux, it.side ** 3, 1.0, 1e-6), steps)
+                b.release(slot)
+                del slots[slot]
+            else:
+                prev[slot] = flux
+    secs = time.perf_counter() - t1
+    b.close()
+    steps = [v[1] for v in done.values()]
+    return {"workload": "64 sphere packs, side U{32..192}, porosity U[0.3,0.8), r = 8 (seed 4), FP32 AA, "
+                        "rounds of 100 steps, retire at relative flux change < 1e-6",
+            "geometries": len(items), "fluid_nodes": int(nodes_total), "admit_s": round(t_admit, 2),
+            "tuned": {"block_size": bs, "nodes_per_thread": npt, "mflups": round(tuned, 1)},
+            "converged": len(done), "unfinished": len(items) - len(done), "solve_wall_s": round(secs, 2),
+            "aggregate_mflups": round(updates / secs / 1e6, 1),
+            "steps_to_converge": {"min": min(steps) if steps else None, "median": float(np.median(steps)) if steps else None,
+                                  "max": max(steps) if steps else None},
+            "k_range": [min(v[0] for v in done.values()), max(v[0] for v in done.values())] if done else None}
+
+
+def run_serving(torch, lbm, args):
+    """Poisson arrivals (20 requests/s, seed 5) of sphere packs with sides
+    U{64..384} and porosity U[0.3, 0.8), r = 8, served by continuous batching
+    with FP16-stored PDFs (FP32 collision, FP64 flux sums) within a 150 GB HBM
+    budget; the first requests also solved one at a time in FP64."""
+    from paper_1111_0922_gb300 import permeability, serving
+
+    budget = 150e9
+    per_slot = lbm.lbm_batch_bytes_per_slot(lbm.LBM_AA, lbm.LBM_F16S)
+    cap = min(int(budget / per_slot), (1 << 31) - 65536)
+    reqs = serving.poisson_requests(args.serve_requests, 20.0, seed=5)
+    offered = sum(int(r.pack.dims[0] ** 3 * r.pack.porosity_target) for r in reqs) / (reqs[-1].arrival or 1.0)
+    eng = serving.BatchEngine(cap, variant="aa", precision="f16s", f16_scale=2.0 ** 26,
+                              max_geometries=len(reqs) + 1)
+    st = serving.serve(reqs, eng, serving.RealClock(), k_round=100, tol=1e-6, max_steps=args.serve_max_steps)
+    eng.close()
+    torch.cuda.empty_cache()
+    summ = st.summary()
+    # FP64, one solve at a time, on the first requests
+    base = []
+    for r in reqs[: args.serve_fp64]:
+        lat = lbm.Lattice(r.pack.dims, r.pack.periodic, variant="aa", addressing="indirect", precision="f64",
+                          omega=r.omega, force=r.force)
+        t0 = time.perf_counter()
+        lat.set_geometry_spheres(r.pack.centres, r.pack.radius, r.pack.unit)
+        lat.init()
+        res = permeability.solve(lat, r.omega, r.force[0], max_steps=args.serve_max_steps)
+        base.append((r.rid, res.k, time.perf_counter() - t0, res.steps))
+        lat.close()
+        torch.cuda.empty_cache()
+    by_id = {x.rid: x for x in st.results}
+    k_err = [abs(by_id[rid].k - k) / k for rid, k, _, _ in base if rid in by_id and by_id[rid].converged]
+    return {"workload": "Poisson 20/s (seed 5), %d requests, side U{64..384}, porosity U[0.3,0.8), r = 8, "
+                        "AA pattern, FP16 storage (S = 2^26), 150 GB budget" % len(reqs),
+            "offered_node_rate_per_s": round(offered, 1), "capacity_slots": cap,
+            **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()},
+            "fp64_one_at_a_time": {"requests": len(base),
+                                   "mean_service_s": round(float(np.mean([b[2] for b in base])), 3) if base else None,
+                                   "solves_per_s": round(len(base) / sum(b[2] for b in base), 4) if base else None,
+                                   "k_rel_err_fp16_vs_fp64_max": max(k_err) if k_err else None}}
+
+
 def main_gb300(args):
     import torch
 
@@ -345,7 +453,7 @@ def main_gb300(args):
     hbm, peak_kind = measured_peaks()
     head = run_headline(torch, lbm, args, rank, world)
     n = head["nodes"]
-    value = world * n * args.steps / head["total_s"] / 1e6
+    value = replica_value(n, args.steps, world, head["total_s"])
     bytes_launch = n * model.kernel_bytes_per_flup("aa", False, "f32")
     achieved = bytes_launch / head["per_launch_s"] / 1e9
     traffic = profiled_traffic("aa_f32_soa_direct_256")
@@ -374,6 +482,12 @@ def main_gb300(args):
         result["variants"] = run_sweep(torch, lbm, args, hbm)
     if rank == 0 and not args.no_sparse:
         result["sparse"] = run_sparse(torch, lbm, args, hbm)
+    if rank == 0 and not args.no_batch:
+        result["batch"] = run_batch(torch, lbm, args)
+        log("batch", result["batch"])
+    if rank == 0 and not args.no_serving:
+        result["serving"] = run_serving(torch, lbm, args)
+        log("serving", result["serving"])
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -432,6 +546,13 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--sparse-steps", type=int, default=50)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-seconds", type=float, default=60.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-fp64", type=int, default=2)
+    ap.add_argument("--serve-max-steps", type=int, default=30000)
     a = ap.parse_args(argv)
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")

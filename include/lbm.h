@@ -186,6 +186,89 @@ lbm_status lbm_macroscopics(lbm_t *h, double *rho, double *u, int on_device);
 /* Wait for the handle's stream and report device-side errors. */
 lbm_status lbm_sync(lbm_t *h);
 
+/* ------------------------------------------------------------------------
+ * Batches: many geometries advanced together (continuous batching).
+ *
+ * Each admitted geometry is a fluid-node list stored as one segment of
+ * shared SoA arrays (segments start on multiples of 4096 slots; IDX entries
+ * are absolute slot numbers).  One launch per time step covers the nodes of
+ * every active geometry, each with its own omega, force and step count, so
+ * geometries admitted at different times run side by side.  A round of k
+ * steps is replayed from a captured CUDA graph; its first step also reduces
+ * each geometry's mass and flux (FP64, per 4096-aligned chunk, then summed in
+ * chunk order), so a geometry's results are bit-identical alone and in any
+ * mix.  Variants: LBM_AA or LBM_ET on node lists, SoA. */
+typedef struct lbm_batch_config {
+  int32_t variant;           /* LBM_AA or LBM_ET */
+  int32_t precision;         /* LBM_F64, LBM_F32, LBM_F16S */
+  int32_t block_size;        /* threads per block, multiple of 32, <= 256; 0 = 256 */
+  int32_t nodes_per_thread;  /* 1, 2, 4 or 8; block_size * nodes_per_thread divides 4096; 0 = 1 */
+  int64_t capacity_slots;    /* node slots of the shared arrays (rounded up to 4096) */
+  int32_t max_geometries;    /* size of the geometry table */
+  int32_t reserved;
+  double f16_scale;          /* LBM_F16S: the power-of-two scale of every geometry */
+  void *stream;              /* cudaStream_t; NULL = default stream */
+  lbm_alloc_fn dev_alloc;    /* optional device allocator, as in lbm_config */
+  lbm_free_fn dev_free;
+  void *alloc_ctx;
+} lbm_batch_config;
+
+typedef struct lbm_batch_info {
+  int64_t capacity_slots;    /* slots per array */
+  int64_t free_slots;        /* unreserved slots */
+  int64_t largest_free;      /* largest contiguous free range */
+  int64_t active_nodes;      /* fluid nodes of the active geometries */
+  int64_t device_bytes;      /* PDF + index arrays */
+  int32_t active_geometries;
+  int32_t block_size;
+  int32_t nodes_per_thread;
+  int32_t work_chunks;       /* blocks of one step launch */
+} lbm_batch_info;
+
+typedef struct lbm_batch lbm_batch_t;
+
+/* Device bytes per node slot of a batch: 19 PDFs + the index words
+ * (18 for LBM_AA, 9 for LBM_ET). */
+int64_t lbm_batch_bytes_per_slot(int32_t variant, int32_t precision);
+
+/* Allocate the shared arrays (capacity_slots x lbm_batch_bytes_per_slot). */
+lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out);
+lbm_status lbm_batch_destroy(lbm_batch_t *b);
+const char *lbm_batch_last_error(const lbm_batch_t *b);
+
+/* Admit a sphere-pack geometry (as lbm_set_geometry_spheres: dims[3],
+ * periodic[3], nsph x 3 centres and radius in 1/unit cells), with its own
+ * omega and force, at rest.  Builds its node list and index on the GPU into
+ * the first free range that fits; LBM_ERR_OOM (nothing changed) when no range
+ * or geometry-table entry is free.  *slot receives its id.  Synchronises. */
+lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const int32_t *periodic, int64_t nsph,
+                                   const int64_t *centres, int64_t radius, int64_t unit, double omega,
+                                   const double *force, int32_t *slot);
+
+/* Free a geometry's range and table entry. */
+lbm_status lbm_batch_release(lbm_batch_t *b, int32_t slot);
+
+/* Enqueue k >= 1 steps of every active geometry (graph replay).  The mass
+ * and flux of each geometry's state at the start of the round become
+ * readable with lbm_batch_poll.  Asynchronous. */
+lbm_status lbm_batch_round(lbm_batch_t *b, int32_t k);
+
+/* Results of the last round for one geometry, and its step count.  Waits for
+ * the round. */
+lbm_status lbm_batch_poll(lbm_batch_t *b, int32_t slot, double *mass, double *flux, int64_t *steps);
+lbm_status lbm_batch_slot_info(lbm_batch_t *b, int32_t slot, int64_t *nodes, int64_t *cells, int64_t *steps);
+lbm_status lbm_batch_get_info(lbm_batch_t *b, lbm_batch_info *info);
+
+/* Natural state of one geometry (19 x nodes FP64, host); LBM_AA requires an
+ * even step count.  Synchronises. */
+lbm_status lbm_batch_get_pdfs(lbm_batch_t *b, int32_t slot, double *f_host);
+
+/* Launch-shape autotuner: times `rounds` rounds of k steps for each
+ * (block size, nodes per thread) candidate with CUDA events and keeps the
+ * fastest.  Advances the active geometries by those steps. */
+lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *best_block_size,
+                          int32_t *best_nodes_per_thread, double *best_mflups);
+
 /* Mass and flux of a caller-owned natural PDF array, with no allocation.
  * (This entry point has no counterpart in the paper.)
  *

@@ -252,6 +252,7 @@ struct DirectNode {
   int cell;   // own cell (solid mask index)
   int dx[2], dy[2], dz[2];
   unsigned wall;  // bit 2a + side: face (axis a, -1 / +1 side) is a wall
+  bool fast;      // no wall face and no solid mask: every neighbour is fluid
 
   __device__ __forceinline__ bool setup(const Grid &g) {
     if (grid_solid(g, x, y, z)) return false;
@@ -270,6 +271,7 @@ struct DirectNode {
     if (y == g.ny - 1) { if (g.py) dy[1] = 1 - g.ny; else wall |= 8u; }
     if (z == 0) { if (g.pz) dz[0] = g.nz - 1; else wall |= 16u; }
     if (z == g.nz - 1) { if (g.pz) dz[1] = 1 - g.nz; else wall |= 32u; }
+    fast = wall == 0 && g.solid == nullptr;
     return true;
   }
   // flat cell index (state kernels)
@@ -302,6 +304,7 @@ struct DirectNode {
     dz[0] = launder(dz[0]);
     dz[1] = launder(dz[1]);
     wall = (unsigned)launder((int)wall);
+    fast = launder((int)fast) != 0;
   }
   // storage slot of x + c_i whether fluid or not (the halo beyond a wall)
   __device__ __forceinline__ int pos(const StepParams &p, int i) const {
@@ -309,6 +312,13 @@ struct DirectNode {
     const int ey = CY(i) < 0 ? dy[0] : (CY(i) > 0 ? dy[1] : 0);
     const int ez = CZ(i) < 0 ? dz[0] : (CZ(i) > 0 ? dz[1] : 0);
     return s + ex + (int)p.g.sx * ey + (int)p.g.sxy * ez;
+  }
+  // neighbour slot when the node is known to be `fast` (never -1)
+  __device__ __forceinline__ int nb_fast(const StepParams &p, int i) const { return pos(p, i); }
+  // FAST selects nb_fast at compile time
+  template <bool FAST>
+  __device__ __forceinline__ int nbf(const StepParams &p, int i) const {
+    return FAST ? nb_fast(p, i) : nb(p, i);
   }
   // slot of the fluid neighbour along c_i, or -1 for a wall or solid link
   __device__ __forceinline__ int nb(const StepParams &p, int i) const {
@@ -337,6 +347,9 @@ struct IndirectNode {
   __device__ static __forceinline__ int64_t it_step(const StepParams &) { return (int64_t)gridDim.x * blockDim.x; }
   __device__ __forceinline__ bool init_it(const StepParams &p, int64_t it) { return init(p, it); }
   __device__ __forceinline__ void launder_all() { s = launder(s); }
+  static constexpr bool fast = false;
+  template <bool FAST>
+  __device__ __forceinline__ int nbf(const StepParams &p, int i) const { return nb(p, i); }
   __device__ __forceinline__ int nb(const StepParams &p, int i) const {
     return __ldg(p.idx + (int64_t)(i - 1) * p.ipad + s);
   }

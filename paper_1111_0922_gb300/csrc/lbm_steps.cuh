@@ -86,55 +86,74 @@ __global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
 }
 
 // One-step push (Fig. 1a,b): read A at the node, write B at the neighbours.
+// FAST: the node has no solid or wall link (no bounce-back branch).
+template <bool FAST, class C, int AOS, class Node, bool FORCE>
+__device__ __forceinline__ void os_push_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
+                                             const Lattice<C, AOS> &B, double &m, double &j) {
+  using T = typename C::T;
+  T d[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
+  run_collision<T, FORCE>(d, p, m, j);
+  nd.launder_all();
+  B.st(0, nd.s, d[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int dst = nd.template nbf<FAST>(p, i);
+    if (FAST || dst >= 0)
+      B.st(i, dst, d[i]);
+    else
+      B.st(OPP(i), nd.s, d[i]);
+  }
+}
+
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_os_push(StepParams p) {
-  using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    T d[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
-    run_collision<T, FORCE>(d, p, m, j);
-    nd.launder_all();
-    B.st(0, nd.s, d[0]);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int dst = nd.nb(p, i);
-      if (dst >= 0)
-        B.st(i, dst, d[i]);
-      else
-        B.st(OPP(i), nd.s, d[i]);
-    }
+    if (nd.fast)
+      os_push_node<true, C, AOS, Node, FORCE>(p, nd, A, B, m, j);
+    else
+      os_push_node<false, C, AOS, Node, FORCE>(p, nd, A, B, m, j);
   }
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
 // One-step pull (Fig. 1c,d): gather from the neighbours in A, write B at the
 // node.  The stored state is post-collision.
+template <bool FAST, class C, int AOS, class Node, bool FORCE>
+__device__ __forceinline__ void os_pull_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
+                                             const Lattice<C, AOS> &B, double &m, double &j) {
+  using T = typename C::T;
+  T d[Q];
+  d[0] = A.ld(0, nd.s);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int src = nd.template nbf<FAST>(p, OPP(i));
+    d[i] = (FAST || src >= 0) ? A.ld(i, src) : A.ld(OPP(i), nd.s);
+  }
+  run_collision<T, FORCE>(d, p, m, j);
+  nd.launder_all();
+#pragma unroll
+  for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
+}
+
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_os_pull(StepParams p) {
-  using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    T d[Q];
-    d[0] = A.ld(0, nd.s);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int src = nd.nb(p, OPP(i));
-      d[i] = src >= 0 ? A.ld(i, src) : A.ld(OPP(i), nd.s);
-    }
-    run_collision<T, FORCE>(d, p, m, j);
-    nd.launder_all();
-#pragma unroll
-    for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
+    if (nd.fast)
+      os_pull_node<true, C, AOS, Node, FORCE>(p, nd, A, B, m, j);
+    else
+      os_pull_node<false, C, AOS, Node, FORCE>(p, nd, A, B, m, j);
   }
   if (RED) block_reduce_store(m, j, p.partials);
 }
@@ -164,40 +183,54 @@ __global__ void LBM_STEP_BOUNDS k_aa_even(StepParams p) {
 // node at x - c_i (own slot i across a solid link); the result goes to slot i
 // of x + c_i (own opposite slot across a solid link).  Every slot written was
 // read by the same thread.
+template <bool FAST, class C, int AOS, class Node, bool FORCE>
+__device__ __forceinline__ void aa_odd_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A, double &m,
+                                            double &j) {
+  using T = typename C::T;
+  // Full-grid neighbours are recomputed after the collision; IDX entries are
+  // loaded again for the stores (L1 hits) unless LBM_AA_HOLD_IDX keeps them
+  // in registers across the collision.
+#ifdef LBM_AA_HOLD_IDX
+  constexpr bool kHold = std::is_same<Node, IndirectNode>::value;
+#else
+  constexpr bool kHold = false;
+#endif
+  int nb[Q];
+  if (kHold) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nb[i] = nd.nb(p, i);
+  }
+  T d[Q];
+  d[0] = A.ld(0, nd.s);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int src = kHold ? nb[OPP(i)] : nd.template nbf<FAST>(p, OPP(i));
+    d[i] = (FAST || src >= 0) ? A.ld(OPP(i), src) : A.ld(i, nd.s);
+  }
+  run_collision<T, FORCE>(d, p, m, j);
+  nd.launder_all();
+  A.st(0, nd.s, d[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int dst = kHold ? nb[i] : nd.template nbf<FAST>(p, i);
+    if (FAST || dst >= 0)
+      A.st(i, dst, d[i]);
+    else
+      A.st(OPP(i), nd.s, d[i]);
+  }
+}
+
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
-  using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    // IDX entries are loaded once and kept; full-grid neighbours are cheap to
-    // recompute after the collision
-    constexpr bool kHold = std::is_same<Node, IndirectNode>::value;
-    int nb[Q];
-    if (kHold) {
-#pragma unroll
-      for (int i = 1; i < Q; ++i) nb[i] = nd.nb(p, i);
-    }
-    T d[Q];
-    d[0] = A.ld(0, nd.s);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int src = kHold ? nb[OPP(i)] : nd.nb(p, OPP(i));
-      d[i] = src >= 0 ? A.ld(OPP(i), src) : A.ld(i, nd.s);
-    }
-    run_collision<T, FORCE>(d, p, m, j);
-    nd.launder_all();
-    A.st(0, nd.s, d[0]);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int dst = kHold ? nb[i] : nd.nb(p, i);
-      if (dst >= 0)
-        A.st(i, dst, d[i]);
-      else
-        A.st(OPP(i), nd.s, d[i]);
-    }
+    if (nd.fast)
+      aa_odd_node<true, C, AOS, Node, FORCE>(p, nd, A, m, j);
+    else
+      aa_odd_node<false, C, AOS, Node, FORCE>(p, nd, A, m, j);
   }
   if (RED) block_reduce_store(m, j, p.partials);
 }
@@ -205,7 +238,9 @@ __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
 // Esoteric-twist helpers on a full grid (unused for node lists).
 __device__ __forceinline__ int et_pos(const DirectNode &nd, const StepParams &p, int i) { return nd.pos(p, i); }
 __device__ __forceinline__ int et_pos(const IndirectNode &nd, const StepParams &, int) { return nd.s; }
-__device__ __forceinline__ bool et_linked(const DirectNode &nd, const StepParams &p, int i) { return nd.nb(p, i) >= 0; }
+__device__ __forceinline__ bool et_linked(const DirectNode &nd, const StepParams &p, int i) {
+  return nd.fast || nd.nb(p, i) >= 0;
+}
 __device__ __forceinline__ bool et_linked(const IndirectNode &, const StepParams &, int) { return true; }
 
 // Esoteric twist (Fig. 6): PDF f_i of node x lives in array map[i] at x for

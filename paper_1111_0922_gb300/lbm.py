@@ -58,6 +58,23 @@ class lbm_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class lbm_batch_config(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
+                ("capacity_slots", ctypes.c_int64), ("max_geometries", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("f16_scale", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class lbm_batch_info(ctypes.Structure):
+    _fields_ = [("capacity_slots", ctypes.c_int64), ("free_slots", ctypes.c_int64),
+                ("largest_free", ctypes.c_int64), ("active_nodes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("active_geometries", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
+                ("work_chunks", ctypes.c_int32)]
+
+
 # exported symbols and their signatures (every function declared in lbm.h)
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -82,6 +99,22 @@ SIGNATURES = {
     "lbm_flux": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "lbm_macroscopics": (_I, [_P, _P, _P, _I]),
     "lbm_sync": (_I, [_P]),
+    "lbm_batch_bytes_per_slot": (_I64, [ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_config), ctypes.POINTER(_P)]),
+    "lbm_batch_destroy": (_I, [_P]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_batch_admit_spheres": (_I, [_P, _P, _P, _I64, _P, _I64, _I64, ctypes.c_double, _P,
+                                     ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_release": (_I, [_P, ctypes.c_int32]),
+    "lbm_batch_round": (_I, [_P, ctypes.c_int32]),
+    "lbm_batch_poll": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_batch_slot_info": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_batch_get_info": (_I, [_P, ctypes.POINTER(lbm_batch_info)]),
+    "lbm_batch_get_pdfs": (_I, [_P, ctypes.c_int32, _P]),
+    "lbm_batch_tune": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "lbm_flux_noalloc": (_I, [_P, ctypes.c_int32, ctypes.c_int32, _I64, _I64, ctypes.c_double,
                               ctypes.c_double, _P, _P]),
 }
@@ -379,3 +412,143 @@ class Lattice:
 
     def sync(self):
         lbm_sync(self.h)
+
+
+# ---------------------------------------------------------------------------
+# Batches (continuous batching of many geometries)
+
+def _bcheck(b, status):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(b)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def lbm_batch_bytes_per_slot(variant, precision):
+    return int(load().lbm_batch_bytes_per_slot(int(variant), int(precision)))
+
+
+def lbm_batch_create(cfg: lbm_batch_config):
+    b = ctypes.c_void_p()
+    _bcheck(None, load().lbm_batch_create(ctypes.byref(cfg), ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_destroy(b):
+    _bcheck(None, load().lbm_batch_destroy(b))
+
+
+def lbm_batch_admit_spheres(b, dims, periodic, centres, radius, unit, omega, force):
+    d = (ctypes.c_int32 * 3)(*[int(v) for v in dims])
+    p = (ctypes.c_int32 * 3)(*[int(v) for v in periodic])
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    c = np.ascontiguousarray(np.asarray(centres, dtype=np.int64).reshape(-1, 3))
+    slot = ctypes.c_int32()
+    _bcheck(b, load().lbm_batch_admit_spheres(b, d, p, c.shape[0], _ptr(c), int(radius), int(unit),
+                                              float(omega), f, ctypes.byref(slot)))
+    return slot.value
+
+
+def lbm_batch_release(b, slot):
+    _bcheck(b, load().lbm_batch_release(b, int(slot)))
+
+
+def lbm_batch_round(b, k):
+    _bcheck(b, load().lbm_batch_round(b, int(k)))
+
+
+def lbm_batch_poll(b, slot):
+    m, f, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _bcheck(b, load().lbm_batch_poll(b, int(slot), ctypes.byref(m), ctypes.byref(f), ctypes.byref(s)))
+    return m.value, f.value, s.value
+
+
+def lbm_batch_slot_info(b, slot):
+    n, c, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _bcheck(b, load().lbm_batch_slot_info(b, int(slot), ctypes.byref(n), ctypes.byref(c), ctypes.byref(s)))
+    return n.value, c.value, s.value
+
+
+def lbm_batch_get_info(b) -> lbm_batch_info:
+    info = lbm_batch_info()
+    _bcheck(b, load().lbm_batch_get_info(b, ctypes.byref(info)))
+    return info
+
+
+def lbm_batch_get_pdfs(b, slot, nodes):
+    out = np.empty((Q, nodes), np.float64)
+    _bcheck(b, load().lbm_batch_get_pdfs(b, int(slot), _ptr(out)))
+    return out
+
+
+def lbm_batch_tune(b, rounds=2, k=10):
+    bs, npt, mf = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _bcheck(b, load().lbm_batch_tune(b, int(rounds), int(k), ctypes.byref(bs), ctypes.byref(npt),
+                                     ctypes.byref(mf)))
+    return bs.value, npt.value, mf.value
+
+
+class Batch:
+    """Many sphere-pack geometries on one GPU, advanced together in rounds."""
+
+    def __init__(self, capacity_slots, variant="aa", precision="f32", max_geometries=1024,
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, stream=None,
+                 use_torch_allocator=True):
+        cfg = lbm_batch_config()
+        cfg.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg.block_size = int(block_size)
+        cfg.nodes_per_thread = int(nodes_per_thread)
+        cfg.capacity_slots = int(capacity_slots)
+        cfg.max_geometries = int(max_geometries)
+        cfg.f16_scale = float(f16_scale)
+        self._alloc = None
+        if stream is None or use_torch_allocator:
+            import torch
+
+            dev = torch.cuda.current_device()
+            if stream is None:
+                stream = torch.cuda.current_stream(dev).cuda_stream
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(dev, stream)
+                cfg.dev_alloc = self._alloc.alloc
+                cfg.dev_free = self._alloc.free
+        cfg.stream = ctypes.c_void_p(int(stream) if stream else 0)
+        self.cfg = cfg
+        self.b = lbm_batch_create(cfg)
+
+    def close(self):
+        if self.b:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def admit(self, pack, omega, force):
+        return lbm_batch_admit_spheres(self.b, pack.dims, pack.periodic, pack.centres, pack.radius,
+                                       pack.unit, omega, force)
+
+    def release(self, slot):
+        lbm_batch_release(self.b, slot)
+
+    def round(self, k):
+        lbm_batch_round(self.b, k)
+
+    def poll(self, slot):
+        return lbm_batch_poll(self.b, slot)
+
+    def slot_info(self, slot):
+        return lbm_batch_slot_info(self.b, slot)
+
+    @property
+    def info(self):
+        return lbm_batch_get_info(self.b)
+
+    def pdfs(self, slot):
+        return lbm_batch_get_pdfs(self.b, slot, self.slot_info(slot)[0])
+
+    def tune(self, rounds=2, k=10):
+        return lbm_batch_tune(self.b, rounds, k)

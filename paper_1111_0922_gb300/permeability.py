@@ -3,7 +3,7 @@
 The flow is advanced in rounds of `check` steps; each round's first kernel
 also reduces (FP64, fixed order) the flux sum(rho u_x) of the state the round
 starts from.  Converged when |Phi_m - Phi_{m-1}| < tol |Phi_m| for two
-consecutive rounds' fluxes.  Darcy: k = nu <rho u_x> / g, the average taken
+consecutive rounds' fluxes; k is taken from Phi_m.  Darcy: k = nu <rho u_x> / g, the average taken
 over every cell of the box (superficial velocity), nu = (1/omega - 1/2)/3.
 """
 from __future__ import annotations
@@ -33,12 +33,11 @@ def solve(lat, omega: float, gx: float, check: int = 100, tol: float = 1e-6,
     cells = int(lat.info.cells)
     prev = None
     steps = 0
+    mass = flux = 0.0
     while steps < max_steps:
-        mass, flux = lat.step_flux(check)
+        mass, flux = lat.step_flux(check)  # flux of the state this round starts from
         steps += check
         if prev is not None and abs(flux - prev) < tol * abs(flux):
-            m2, f2 = lat.flux()
-            return Solve(permeability(f2, cells, omega, gx), f2, m2, steps, True)
+            return Solve(permeability(flux, cells, omega, gx), flux, mass, steps, True)
         prev = flux
-    m2, f2 = lat.flux()
-    return Solve(permeability(f2, cells, omega, gx), f2, m2, steps, False)
+    return Solve(permeability(flux, cells, omega, gx), flux, mass, steps, False)

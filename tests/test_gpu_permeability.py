@@ -24,13 +24,12 @@ def pack_and_oracle():
     f = oracle.rest_state(cells.size)
     prev, steps = None, 0
     while steps < 200000:
-        _, phi = oracle.flux(f, (GX, 0, 0))
+        _, phi = oracle.flux(f, (GX, 0, 0))  # state at the start of the round
         f = oracle.run_sparse(idx, f, 100, OMEGA, (GX, 0, 0))
         steps += 100
         if prev is not None and abs(phi - prev) < 1e-6 * abs(phi):
             break
         prev = phi
-    _, phi = oracle.flux(f, (GX, 0, 0))
     k = oracle.permeability(phi, int(np.prod(DIMS)), OMEGA, GX)
     return pack, k, steps
 
