@@ -94,7 +94,8 @@ typedef struct lbm_config {
   int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128 */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default */
   int32_t cg_shift;          /* LBM_CG: shift k in planes (direct) >= 2; 0 = default */
-  int32_t reserved;
+  int32_t pair_x;            /* LBM_AA, full grid, SoA: 0 = two x-adjacent nodes per thread where
+                                possible (periodic x, even nx, no solid cell), 1 = one node per thread */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

@@ -200,6 +200,27 @@ static LaunchShape shape_of(const lbm_t *h) {
 
 static int64_t blocks_of(const LaunchShape &L) { return (int64_t)L.grid.x * L.grid.y * L.grid.z; }
 
+// AA pattern with two x-adjacent nodes per thread (lbm_pair.cuh)?
+static bool use_pairs(const lbm_t *h) {
+  const lbm_config &c = h->cfg;
+  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 0 &&
+         c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
+}
+
+static LaunchShape pair_shape_of(const lbm_t *h) {
+  LaunchShape L;
+  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
+  const int npairs = h->cfg.nx / 2;
+  const int bx = (int)std::min<int64_t>(bs, round_up(npairs, 32));
+  const int by = std::max(1, bs / bx);
+  L.grid = dim3((unsigned)((npairs + bx - 1) / bx), (unsigned)((h->cfg.ny + by - 1) / by),
+                (unsigned)std::min<int64_t>((h->cfg.nz + npt - 1) / npt, 65535));
+  L.block = dim3((unsigned)bx, (unsigned)by);
+  L.stream = h->stream;
+  return L;
+}
+
 static SwapTiles swap_tiles(const lbm_t *h) {
   SwapTiles t;
   t.tx = std::min(32, h->cfg.nx);
@@ -286,6 +307,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   }
   if (cfg->dev_alloc && !cfg->dev_free) return fail(nullptr, LBM_ERR_INVALID_ARG, "dev_alloc without dev_free");
   if (cfg->cg_shift != 0 && cfg->cg_shift < 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift must be >= 2");
+  if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
   if (cfg->variant == LBM_CG && cfg->addressing == LBM_INDIRECT)
     return fail(nullptr, LBM_ERR_UNSUPPORTED, "compressed grid runs on direct addressing only in this build");
   if (cfg->variant == LBM_SWAP && cfg->addressing == LBM_INDIRECT)
@@ -851,7 +873,13 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
     }
     case LBM_AA: {
       StepParams p = params_of(h);
-      launch_step_kernel(VAR_AA, (int)(h->steps & 1), p, k, L);
+      if (use_pairs(h)) {
+        const LaunchShape L2 = pair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_AA, 2 + (int)(h->steps & 1), p, k, L2);
+      } else {
+        launch_step_kernel(VAR_AA, (int)(h->steps & 1), p, k, L);
+      }
       break;
     }
     case LBM_ET: {

@@ -9,6 +9,7 @@
 
 #include "lbm_dispatch.cuh"
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 
 namespace lbmk {
 
@@ -28,7 +29,16 @@ __device__ __forceinline__ Lattice<C, AOS> lattice_of(void *p, const StepParams 
 #ifndef LBM_STEP_MAXT
 #define LBM_STEP_MAXT 256
 #endif
-#define LBM_STEP_BOUNDS __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks)
+// Node-list kernels get one more resident block in FP32/FP16 (64 registers):
+// their PDF loads wait for IDX loads, two memory round trips per node, so
+// they need more warps in flight to cover HBM latency.
+template <class C, bool IND>
+constexpr int step_min_blocks() {
+  return (IND && C::kMinBlocks == 3) ? 4 : C::kMinBlocks;
+}
+#define LBM_STEP_BOUNDS \
+  __launch_bounds__(LBM_STEP_MAXT, (step_min_blocks<C, std::is_same<Node, IndirectNode>::value>()))
+#define LBM_STEP_BOUNDS_IND __launch_bounds__(LBM_STEP_MAXT, (step_min_blocks<C, IND>()))
 
 template <bool IND>
 using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
@@ -254,7 +264,7 @@ __device__ __forceinline__ bool et_linked(const IndirectNode &, const StepParams
 //             slot of x + c_{2k+1} in bits 0..30 (a ghost slot >= nfluid when
 //             that cell is solid) and in bit 31 whether x + c_{2k+2} is solid.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void LBM_STEP_BOUNDS k_et(StepParams p) {
+__global__ void LBM_STEP_BOUNDS_IND k_et(StepParams p) {
   using T = typename C::T;
   using Node = NodeOf<IND>;
   const auto A = lattice_of<C, AOS>(p.A, p);
@@ -326,10 +336,20 @@ struct LaunchOS {
       k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
+// sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
-  static void run(const StepParams &p, int odd, const LaunchShape &L) {
-    if (odd)
+  static void run(const StepParams &p, int sub, const LaunchShape &L) {
+    if (sub >= 2) {
+      if constexpr (AOS == 0 && !IND) {
+        if (sub == 3)
+          k_aa2_odd<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+        else
+          k_aa2_even<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      }
+      return;
+    }
+    if (sub)
       k_aa_odd<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
     else
       k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);

@@ -44,7 +44,7 @@ class lbm_config(ctypes.Structure):
                 ("omega", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("f16_scale", ctypes.c_double),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
-                ("cg_shift", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cg_shift", ctypes.c_int32), ("pair_x", ctypes.c_int32),
                 ("stream", ctypes.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
@@ -318,7 +318,7 @@ class Lattice:
 
     def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
                  layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
-                 f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0,
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0, pair_x=0,
                  stream=None, use_torch_allocator=True):
         self.cfg = lbm_config_default()
         c = self.cfg
@@ -336,6 +336,7 @@ class Lattice:
         c.block_size = int(block_size)
         c.nodes_per_thread = int(nodes_per_thread)
         c.cg_shift = int(cg_shift)
+        c.pair_x = int(pair_x)
         self._alloc = None
         if stream is None or use_torch_allocator:
             import torch

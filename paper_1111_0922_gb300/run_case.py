@@ -39,7 +39,7 @@ def setup(args):
     dims = (size, size, size)
     common = dict(variant=args.variant, addressing=args.addressing, layout=args.layout,
                   precision=args.precision, block_size=args.block_size,
-                  nodes_per_thread=args.nodes_per_thread)
+                  nodes_per_thread=args.nodes_per_thread, pair_x=args.pair_x)
     if kind == "dense":
         lat = lbm.Lattice(dims, (1, 1, 1), omega=1.7, **common)
         lat.set_geometry(None)
@@ -72,6 +72,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--nodes-per-thread", type=int, default=0)
+    ap.add_argument("--pair-x", type=int, default=0, help="AA on a full grid: 0 = x pairs where possible, 1 = off")
     args = ap.parse_args(argv)
     import torch
 

@@ -46,7 +46,10 @@ def test_batch_matches_oracle(L, variant, precision):
         m0, j0 = oracle.flux(f0, g)
         m, j, steps = b.poll(s)
         assert steps == 6
-        assert abs(m - m0) <= 1e-12 * m0 and abs(j - j0) <= 1e-12 * max(abs(j0), 1e-30) + 1e-18
+        # the fused sums add per-node moments from the collision, computed in
+        # the storage's arithmetic (FP32: ~6e-8 relative each), in FP64
+        tol = 1e-12 if precision == "f64" else 1e-6
+        assert abs(m - m0) <= tol * m0 and abs(j - j0) <= tol * abs(j0)
         if precision == "f64":
             assert np.max(np.abs(got - ref) / ref) <= 1e-12
         else:
