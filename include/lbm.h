@@ -1,8 +1,9 @@
 /*
  * liblbm — GB300 (sm_103a) D3Q19 lattice Boltzmann time step, C ABI.
  *
- * One time step is the BGK collision (with a constant body force, Guo's
- * forcing term) at every fluid node followed by the propagation of the
+ * One time step is the BGK collision, or the two-relaxation-time (TRT)
+ * collision of the paper's solver (Sec. 10), with a constant body force
+ * (Guo's forcing term) at every fluid node, followed by the propagation of the
  * post-collision PDFs to the neighbours, with half-way bounce-back at solid
  * nodes and at non-periodic box faces.  The propagation is done by one of the
  * schemes compared by Wittmann, Zeiser, Hager and Wellein, "Comparison of
@@ -91,11 +92,15 @@ typedef struct lbm_config {
   double omega;              /* BGK relaxation rate, 0 < omega < 2 (0 = identity collision) */
   double force[3];           /* body acceleration g (Guo forcing) */
   double f16_scale;          /* LBM_F16S: scale S (power of two); 0 = choose from force */
+  double trt_magic;          /* 0 = BGK; > 0 = two-relaxation-time collision with magic parameter
+                                Lam = (1/omega - 1/2)(1/omega_minus - 1/2), e.g. 3/16 (walls exactly
+                                half-way for Poiseuille flow) */
   int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128 */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default */
   int32_t cg_shift;          /* LBM_CG: shift k in planes (direct) >= 2; 0 = default */
-  int32_t pair_x;            /* LBM_AA, full grid, SoA: 0 = two x-adjacent nodes per thread where
-                                possible (periodic x, even nx, no solid cell), 1 = one node per thread */
+  int32_t pair_x;            /* LBM_AA, full grid, SoA: 1 = two x-adjacent nodes per thread with vector
+                                accesses where possible (periodic x, even nx, no solid cell);
+                                0 = one node per thread (default, faster on GB300) */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

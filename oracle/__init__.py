@@ -74,6 +74,9 @@ def _load():
             "ora_run_variant": (I, [I, P, P, P, P, P, I, D, P]),
             "ora_run_push_full": (None, [P, P, P, P, I, D, P, I]),
             "ora_run_push_sparse": (None, [I64, P, P, I, D, P, I]),
+            "ora_collide_trt": (None, [P, D, D, P, P]),
+            "ora_trt_lambda_minus": (D, [D, D]),
+            "ora_run_push_full_trt": (None, [P, P, P, P, I, D, D, P, I]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -124,6 +127,31 @@ def collide(f, omega, g=(0.0, 0.0, 0.0)):
     gv = _vec3(g)
     lib.ora_collide(_p(f), float(omega), _p(gv), _p(out))
     return out
+
+
+def collide_trt(f, lam_p, lam_m, g=(0.0, 0.0, 0.0)):
+    """Post-collision PDFs of one node with the two-relaxation-time model."""
+    lib = _load()
+    f = np.ascontiguousarray(np.asarray(f, np.float64).reshape(Q))
+    out = np.zeros(Q)
+    gv = _vec3(g)
+    lib.ora_collide_trt(_p(f), float(lam_p), float(lam_m), _p(gv), _p(out))
+    return out
+
+
+def trt_lambda_minus(lam_p, magic=3.0 / 16.0):
+    return float(_load().ora_trt_lambda_minus(float(lam_p), float(magic)))
+
+
+def run_push_trt(dims, periodic, solid, f, nsteps, lam_p, lam_m, g=(0.0, 0.0, 0.0), nthreads=None):
+    """nsteps of the definition with the TRT collision on a full grid."""
+    lib = _load()
+    n = int(np.prod(dims))
+    f = np.array(np.asarray(f, np.float64).reshape(Q, n), order="C", copy=True)
+    gv = _vec3(g)
+    lib.ora_run_push_full_trt(_p(_dims(dims)), _p(_dims(periodic)), _p(_mask(solid, n)), _p(f), int(nsteps),
+                              float(lam_p), float(lam_m), _p(gv), int(nthreads or default_threads()))
+    return f
 
 
 def equilibrium(rho, u):

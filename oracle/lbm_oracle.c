@@ -89,6 +89,50 @@ void ora_collide(const double *f, double omega, const double *g, double *out) {
   }
 }
 
+/* Two-relaxation-time collision (TRT, the paper's solver, Sec. 10 and its
+ * ref. [15]).  Each opposite pair (i, opp i) is split into its symmetric half
+ * f+ = (f_i + f_opp)/2 and antisymmetric half f- = (f_i - f_opp)/2; the
+ * symmetric halves relax towards feq+ with rate lam_p (sets the viscosity),
+ * the antisymmetric halves towards feq- with rate lam_m.  The Guo forcing term
+ * is split the same way, its symmetric half weighted by (1 - lam_p/2) and its
+ * antisymmetric half by (1 - lam_m/2).  lam_m = lam_p is BGK. */
+void ora_collide_trt(const double *f, double lam_p, double lam_m, const double *g, double *out) {
+  double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    jx += CX[i] * f[i];
+    jy += CY[i] * f[i];
+    jz += CZ[i] * f[i];
+  }
+  double ux = (jx + 0.5 * rho * g[0]) / rho;
+  double uy = (jy + 0.5 * rho * g[1]) / rho;
+  double uz = (jz + 0.5 * rho * g[2]) / rho;
+  double usq = ux * ux + uy * uy + uz * uz;
+  double ug = ux * g[0] + uy * g[1] + uz * g[2];
+  double feq[Q], fs[Q], fa[Q];
+  for (int i = 0; i < Q; ++i) {
+    double cu = CX[i] * ux + CY[i] * uy + CZ[i] * uz;
+    double cg = CX[i] * g[0] + CY[i] * g[1] + CZ[i] * g[2];
+    feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    /* Guo term, split into its parts even and odd in c_i */
+    fs[i] = W[i] * rho * (9.0 * cu * cg - 3.0 * ug);
+    fa[i] = W[i] * rho * 3.0 * cg;
+  }
+  for (int i = 0; i < Q; ++i) {
+    int o = opp(i);
+    double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+    double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+    out[i] = f[i] - lam_p * (fp - ep) - lam_m * (fm - em) + (1.0 - 0.5 * lam_p) * fs[i] +
+             (1.0 - 0.5 * lam_m) * fa[i];
+  }
+}
+
+/* Antisymmetric rate from the symmetric one and the "magic" parameter
+ * Lam = (1/lam_p - 1/2)(1/lam_m - 1/2). */
+double ora_trt_lambda_minus(double lam_p, double magic) {
+  return 1.0 / (0.5 + magic / (1.0 / lam_p - 0.5));
+}
+
 /* Density and velocity of one node (the velocity includes the half force). */
 void ora_node_moments(const double *f, const double *g, double *rho_out, double *u_out) {
   double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
@@ -770,6 +814,43 @@ int ora_run_variant(int variant, const int *dims, const int *periodic, const uin
   free(A);
   free(B);
   return rc;
+}
+
+/* One step of the definition with the TRT collision (full grid). */
+void ora_push_full_trt(const int *dims, const int *periodic, const uint8_t *solid, const double *fin,
+                       double *fout, double lam_p, double lam_m, const double *g, int nthreads) {
+  box_t b = make_box(dims, periodic, solid);
+  int64_t n = ncells(&b);
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int64_t c = 0; c < n; ++c) {
+    if (!is_fluid(&b, c)) {
+      for (int i = 0; i < Q; ++i) fout[i * n + c] = fin[i * n + c];
+      continue;
+    }
+    double f[Q], fs[Q];
+    for (int i = 0; i < Q; ++i) f[i] = fin[i * n + c];
+    ora_collide_trt(f, lam_p, lam_m, g, fs);
+    for (int i = 0; i < Q; ++i) {
+      int64_t d = (i == 0) ? c : neighbour(&b, c, i);
+      if (d >= 0)
+        fout[i * n + d] = fs[i];
+      else
+        fout[opp(i) * n + c] = fs[i];
+    }
+  }
+}
+
+void ora_run_push_full_trt(const int *dims, const int *periodic, const uint8_t *solid, double *f, int nsteps,
+                           double lam_p, double lam_m, const double *g, int nthreads) {
+  box_t b = make_box(dims, periodic, solid);
+  size_t bytes = sizeof(double) * Q * (size_t)ncells(&b);
+  double *tmp = (double *)malloc(bytes);
+  for (int t = 0; t < nsteps; ++t) {
+    ora_push_full_trt(dims, periodic, solid, f, tmp, lam_p, lam_m, g, nthreads);
+    memcpy(f, tmp, bytes);
+  }
+  free(tmp);
 }
 
 /* nsteps of the definition, the state kept in f (natural, in place). */

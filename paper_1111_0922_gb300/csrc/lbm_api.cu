@@ -45,6 +45,10 @@ struct lbm {
   int64_t steps = 0;
   float scale = 1.0f;
   int cg_k = 0, cg_o = 0;
+  // compressed grid on a node list: unwrapped index, plane node counts,
+  // shift K (nodes), slab size B, lower ghost room G
+  int32_t *d_cidx = nullptr;
+  int64_t cg_nfirst = 0, cg_nlast = 0, cg_K = 0, cg_B = 0, cg_G = 0;
   int swap_tile[3] = {0, 0, 0};
 };
 
@@ -122,6 +126,7 @@ static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 static size_t store_size(int precision) { return precision == LBM_F64 ? 8 : (precision == LBM_F32 ? 4 : 2); }
 
+
 static bool two_lattices(int variant) {
   return variant == LBM_TS || variant == LBM_OS_PUSH || variant == LBM_OS_PULL;
 }
@@ -150,10 +155,31 @@ static KernelKey key_of(const lbm_t *h, bool red) {
   return k;
 }
 
+static size_t store_size(int precision);
+
+// Element offset of the current state in an indirect compressed grid.
+static int64_t cg_ind_offset(const lbm_t *h, int64_t o) {
+  const int64_t e = o + h->cg_G;
+  return h->cfg.layout == LBM_AOS ? e * Q : e;
+}
+
+static void *shifted(void *base, int64_t elements, int precision) {
+  return static_cast<char *>(base) + elements * (int64_t)store_size(precision);
+}
+
+// Antisymmetric relaxation rate: omega for BGK; for TRT the rate that gives
+// (1/omega - 1/2)(1/omega_m - 1/2) = trt_magic.
+static double omega_minus(const lbm_config &c) {
+  if (!(c.trt_magic > 0.0) || c.omega <= 0.0) return c.omega;
+  return 1.0 / (0.5 + c.trt_magic / (1.0 / c.omega - 0.5));
+}
+
 static StepParams params_of(const lbm_t *h) {
   StepParams p;
   memset(&p, 0, sizeof p);
   p.A = h->d_A;
+  if (h->cfg.variant == LBM_CG && h->cfg.addressing == LBM_INDIRECT && h->d_A)
+    p.A = shifted(h->d_A, cg_ind_offset(h, h->cg_o), h->cfg.precision);
   p.B = h->d_B;
   p.npad = h->npad;
   p.nnodes = h->nn;
@@ -163,6 +189,7 @@ static StepParams params_of(const lbm_t *h) {
   p.ipad = h->ipad;
   for (int i = 0; i < Q; ++i) p.map[i] = h->map[i];
   p.omega = h->cfg.omega;
+  p.omega_m = omega_minus(h->cfg);
   p.gx = h->cfg.force[0];
   p.gy = h->cfg.force[1];
   p.gz = h->cfg.force[2];
@@ -203,7 +230,7 @@ static int64_t blocks_of(const LaunchShape &L) { return (int64_t)L.grid.x * L.gr
 // AA pattern with two x-adjacent nodes per thread (lbm_pair.cuh)?
 static bool use_pairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
-  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 0 &&
+  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 1 &&
          c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
 }
 
@@ -299,6 +326,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
     return fail(nullptr, LBM_ERR_INVALID_ARG, "block_size must be a multiple of 32 in [32, 256]");
   if (cfg->nodes_per_thread < 0 || cfg->nodes_per_thread > 16)
     return fail(nullptr, LBM_ERR_INVALID_ARG, "nodes_per_thread must be in [0, 16]");
+  if (cfg->trt_magic < 0.0 || !std::isfinite(cfg->trt_magic)) return fail(nullptr, LBM_ERR_INVALID_ARG, "trt_magic");
+  if (cfg->trt_magic > 0.0 && !(cfg->omega > 0.0)) return fail(nullptr, LBM_ERR_INVALID_ARG, "TRT needs omega > 0");
   if (cfg->f16_scale < 0.0 || !std::isfinite(cfg->f16_scale))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "f16_scale");
   if (cfg->f16_scale > 0.0) {
@@ -308,10 +337,6 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->dev_alloc && !cfg->dev_free) return fail(nullptr, LBM_ERR_INVALID_ARG, "dev_alloc without dev_free");
   if (cfg->cg_shift != 0 && cfg->cg_shift < 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift must be >= 2");
   if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
-  if (cfg->variant == LBM_CG && cfg->addressing == LBM_INDIRECT)
-    return fail(nullptr, LBM_ERR_UNSUPPORTED, "compressed grid runs on direct addressing only in this build");
-  if (cfg->variant == LBM_SWAP && cfg->addressing == LBM_INDIRECT)
-    return fail(nullptr, LBM_ERR_UNSUPPORTED, "swap runs on direct addressing only in this build");
 
   lbm_t *h = new lbm_t();
   h->cfg = *cfg;
@@ -420,6 +445,27 @@ static lbm_status build_geometry(lbm_t *h) {
       h->nghost = G;
     }
     h->slots = N + h->nghost;
+    if (c.variant == LBM_CG) {
+      h->d_cidx = static_cast<int32_t *>(dalloc(h, sizeof(int32_t) * 18 * h->ipad, h->geo_allocs));
+      int *counters = static_cast<int *>(dalloc(h, sizeof(int) * 4, temps));
+      if (!h->d_cidx || !counters) {
+        cleanup();
+        return fail(h, LBM_ERR_OOM, "compressed-grid index");
+      }
+      h->index_bytes += (int64_t)sizeof(int32_t) * 18 * h->ipad;
+      CUDA_TRY(h, cudaMemsetAsync(counters, 0, sizeof(int) * 4, h->stream));
+      launch_cg_ind_prep(h->d_idx, h->ipad, h->d_cells, N, c.nx, c.ny, c.nz, h->d_cidx, counters, h->stream);
+      int hc[4];
+      CUDA_TRY(h, cudaMemcpyAsync(hc, counters, sizeof hc, cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+      const int64_t D = hc[0];
+      h->cg_nfirst = c.periodic[2] ? hc[1] : 0;
+      h->cg_nlast = c.periodic[2] ? hc[2] : 0;
+      h->cg_B = c.cg_shift > 0 ? c.cg_shift : std::min<int64_t>(std::max<int64_t>(N, 1), (int64_t)1 << 21);
+      h->cg_K = D + h->cg_B;
+      h->cg_G = h->cg_nlast;
+      h->slots = N + h->cg_nfirst + h->cg_nlast + h->cg_K;
+    }
     if (h->slots >= ((int64_t)1 << 31) - 1) {
       cleanup();
       return fail(h, LBM_ERR_INVALID_ARG, "too many storage slots");
@@ -475,7 +521,10 @@ static lbm_status build_geometry(lbm_t *h) {
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
   int64_t need = std::max<int64_t>(blocks_of(L), reduce_blocks_for(h->nn));
-  if (c.variant == LBM_CG) need += (c.nz + h->cg_k - 2) / (h->cg_k - 1) + 1;  // one partial tile per slab
+  if (c.variant == LBM_CG && c.addressing == LBM_DIRECT)
+    need = std::max<int64_t>(need, (int64_t)L.grid.x * L.grid.y * c.nz);  // slabs, 1 plane per z-block
+  if (c.variant == LBM_CG && c.addressing == LBM_INDIRECT)
+    need += (h->nodes + h->cg_B - 1) / std::max<int64_t>(h->cg_B, 1) + 1;  // one partial block per slab
   if (c.variant == LBM_SWAP) {
     const SwapTiles t = swap_tiles(h);
     need = std::max<int64_t>(need, (int64_t)t.ntx * t.nty * t.ntz);
@@ -491,7 +540,8 @@ static void reset_geometry(lbm_t *h) {
   cudaStreamSynchronize(h->stream);
   free_list(h, h->geo_allocs);
   h->d_solid = nullptr;
-  h->d_cells = h->d_idx = h->d_etidx = nullptr;
+  h->d_cells = h->d_idx = h->d_etidx = h->d_cidx = nullptr;
+  h->cg_nfirst = h->cg_nlast = h->cg_K = h->cg_B = h->cg_G = 0;
   h->d_A = h->d_B = nullptr;
   h->d_partials = nullptr;
   h->has_geometry = false;
@@ -606,10 +656,12 @@ static int kernels_per_step(const lbm_t *h) {
   switch (h->cfg.variant) {
     case LBM_TS: return 2;
     case LBM_CG: {
+      if (h->cfg.addressing == LBM_INDIRECT)
+        return (int)((h->nodes + h->cg_B - 1) / std::max<int64_t>(h->cg_B, 1)) + (h->cfg.periodic[2] ? 1 : 0);
       const int slab = h->cg_k - 1;
       return (h->cfg.nz + slab - 1) / slab + (h->cfg.periodic[2] ? 1 : 0);
     }
-    case LBM_SWAP: return swap_tiles(h).ncolours;
+    case LBM_SWAP: return h->cfg.addressing == LBM_INDIRECT ? 2 : swap_tiles(h).ncolours;
     default: return 1;
   }
 }
@@ -798,15 +850,54 @@ lbm_status lbm_flux(lbm_t *h, double *mass, double *jx) {
 // Compressed grid: ghost planes (periodic z), then slabs of k-1 planes in
 // the order that keeps every overwritten plane's readers in earlier slabs.
 // Returns the number of reduction partials written when red.
+static lbm_status cg_step_indirect(lbm_t *h, bool red, int *red_blocks) {
+  const KernelKey k = key_of(h, red);
+  StepParams p = params_of(h);
+  const int64_t o_old = h->cg_o, o_new = o_old == 0 ? h->cg_K : 0;
+  void *A_old = shifted(h->d_A, cg_ind_offset(h, o_old), h->cfg.precision);
+  void *A_new = shifted(h->d_A, cg_ind_offset(h, o_new), h->cfg.precision);
+  if (h->cfg.periodic[2])
+    launch_cg_ind_ghost(A_old, h->npad, h->cfg.precision, h->cfg.layout == LBM_AOS, h->nodes, h->cg_nfirst,
+                        h->cg_nlast, h->stream);
+  p.A = A_old;
+  p.B = A_new;
+  p.idx = h->d_cidx;
+  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
+  const int64_t N = h->nodes, B = std::max<int64_t>(h->cg_B, 1);
+  const int64_t nslab = (N + B - 1) / B;
+  int used = 0;
+  for (int64_t sl = 0; sl < nslab; ++sl) {
+    int64_t a, b;
+    if (o_new > o_old) {  // descending
+      b = N - sl * B;
+      a = std::max<int64_t>(0, b - B);
+    } else {
+      a = sl * B;
+      b = std::min<int64_t>(N, a + B);
+    }
+    p.slab0 = a;
+    p.slab1 = b;
+    LaunchShape L;
+    L.grid = dim3((unsigned)std::max<int64_t>(1, (b - a + (int64_t)bs * npt - 1) / ((int64_t)bs * npt)));
+    L.block = dim3(bs);
+    L.stream = h->stream;
+    p.partials = h->d_partials + 2 * used;
+    launch_cg_ind_slab(p, k, L);
+    used += (int)L.grid.x;
+  }
+  h->cg_o = (int)o_new;
+  if (red_blocks) *red_blocks = used;
+  return LBM_OK;
+}
+
 static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
+  if (h->cfg.addressing == LBM_INDIRECT) return cg_step_indirect(h, red, red_blocks);
   const KernelKey k = key_of(h, red);
   StepParams p = params_of(h);
   const int o_old = h->cg_o, o_new = o_old == 0 ? h->cg_k : 0;
   if (h->cfg.periodic[2]) launch_cg_ghost(p, h->cfg.precision, h->cfg.layout == LBM_AOS, o_old, h->stream);
   const int slab = h->cg_k - 1, nz = h->cfg.nz;
-  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 256;
-  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
-  const int64_t plane = (int64_t)h->cfg.nx * h->cfg.ny;
   p.zo_read = o_old;
   p.zo_write = o_new;
   int used = 0;
@@ -822,14 +913,11 @@ static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
     }
     p.z0 = z0;
     p.z1 = z1;
-    LaunchShape L;
-    const int64_t cnt = plane * (z1 - z0);
-    L.grid = dim3((unsigned)std::max<int64_t>(1, (cnt + (int64_t)bs * npt - 1) / ((int64_t)bs * npt)));
-    L.block = dim3(bs);
-    L.stream = h->stream;
+    LaunchShape L = shape_of(h);
+    L.grid.z = (unsigned)std::min<int64_t>(z1 - z0, 65535);
     p.partials = h->d_partials + 2 * used;
     launch_step_kernel_cg(p, k, L);
-    used += (int)L.grid.x;
+    used += (int)blocks_of(L);
   }
   h->cg_o = o_new;
   h->grid.zoff = o_new;
@@ -840,6 +928,15 @@ static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
 static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
   const KernelKey k = key_of(h, red);
   StepParams p = params_of(h);
+  if (h->cfg.addressing == LBM_INDIRECT) {
+    // collide into the reversed slots (the AA pattern's even kernel), then
+    // exchange the PDFs of every link
+    const LaunchShape L = shape_of(h);
+    launch_step_kernel(VAR_AA, 0, p, k, L);
+    launch_swap_links(p, h->cfg.precision, h->cfg.layout == LBM_AOS, h->stream);
+    if (red_blocks) *red_blocks = (int)blocks_of(L);
+    return LBM_OK;
+  }
   SwapTiles t = swap_tiles(h);
   int used = 0;
   for (int c = 0; c < t.ncolours; ++c) {

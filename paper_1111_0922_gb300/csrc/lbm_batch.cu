@@ -31,6 +31,7 @@ constexpr int64_t kAlign = 4096;  // segment alignment in slots
 
 struct BatchSlot {
   double omega, gx, gy, gz;
+  double omega_m;   // antisymmetric rate (TRT); equal to omega for BGK
   int64_t start;    // first slot of the segment
   int64_t nodes;    // fluid nodes
   int64_t steps;    // steps done before the current round
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
   const BatchSlot &sl = p.slots[w.x];
   const int64_t end = sl.start + sl.nodes;
   const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const T omega = T(sl.omega), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
+  const T omega = T(sl.omega), omega_m = T(sl.omega_m), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
   double m = 0.0, j = 0.0;
 #pragma unroll
   for (int r = 0; r < NPT; ++r) {
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
     if (!odd) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) d[i] = A.ld(i, s);
-      collide<T, true>(d, omega, gx, gy, gz, drho, rjx);
+      collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
       const int s2 = launder(s);
 #pragma unroll
       for (int i = 0; i < Q; ++i) A.st(OPP(i), s2, d[i]);
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
         const int src = __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.npad + s);
         d[i] = src >= 0 ? A.ld(OPP(i), src) : A.ld(i, s);
       }
-      collide<T, true>(d, omega, gx, gy, gz, drho, rjx);
+      collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
       const int s2 = launder(s);
       A.st(0, s2, d[0]);
 #pragma unroll
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_et(BatchParams p) 
   const BatchSlot &sl = p.slots[w.x];
   const int64_t end = sl.start + sl.nodes;
   const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const T omega = T(sl.omega), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
+  const T omega = T(sl.omega), omega_m = T(sl.omega_m), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
   double m = 0.0, j = 0.0;
 #pragma unroll
   for (int r = 0; r < NPT; ++r) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_et(BatchParams p) 
       d[i + 1] = A.ld(ai1, (int)(wd[k] & 0x7fffffffu));
     }
     T drho, rjx;
-    collide<T, true>(d, omega, gx, gy, gz, drho, rjx);
+    collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
     const int s2 = launder(s);
 #pragma unroll
     for (int k = 1; k <= 9; ++k) wd[k] = (uint32_t)launder((int)wd[k]);
@@ -577,6 +578,7 @@ lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const in
   BatchSlot &sl = b->slots[slot];
   memset(&sl, 0, sizeof sl);
   sl.omega = omega;
+  sl.omega_m = omega;
   sl.gx = force[0];
   sl.gy = force[1];
   sl.gz = force[2];

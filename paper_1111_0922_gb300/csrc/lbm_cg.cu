@@ -1,4 +1,5 @@
 // Compressed grid (Sec. 4, Fig. 2, Tab. 3) on a full grid, pull form.
+// (Kernels use DirectNode from lbm_core.cuh.)
 //
 // The paper shifts the whole lattice by one cell per axis between steps and
 // sweeps serially, alternating the sweep direction.  A serial sweep cannot
@@ -19,46 +20,53 @@
 
 namespace lbmk {
 
-template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_cg_slab(StepParams p) {
+// Resident blocks per SM of the node-list slab kernel (as the other node-list
+// kernels: one more block than the full-grid ones in FP32/FP16).
+template <class C>
+constexpr int step_min_cg() {
+  return C::kMinBlocks == 3 ? 4 : C::kMinBlocks;
+}
+
+// One node of a slab: gather at the old offset (the grid's zoff), collide,
+// store at the new offset.  FAST: no wall or solid link.
+template <bool FAST, class C, int AOS, bool FORCE>
+__device__ __forceinline__ void cg_node(const StepParams &p, DirectNode &nd, const Lattice<C, AOS> &A,
+                                        int64_t shift, double &m, double &j) {
   using T = typename C::T;
-  Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
-  const Grid &g = p.g;
-  const int64_t plane = (int64_t)g.nx * g.ny;
-  const int64_t count = plane * (p.z1 - p.z0);
-  double m = 0.0, jsum = 0.0;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < count; n += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(n % g.nx);
-    const int y = (int)((n / g.nx) % g.ny);
-    const int z = p.z0 + (int)(n / plane);
-    if (grid_solid(g, x, y, z)) continue;
-    const int64_t own_old = (x + g.hx) + g.sx * (int64_t)(y + g.hy) + g.sxy * ((int64_t)z + g.hz + p.zo_read);
-    T d[Q];
-    d[0] = L.ld(0, own_old);
+  T d[Q];
+  d[0] = A.ld(0, nd.s);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      // source x - c_i; z unwrapped (the ghost planes hold the periodic copy)
-      int a = x - CX(i), b = y - CY(i), c = z - CZ(i);
-      bool ok = wrap_axis(a, g.nx, g.px) && wrap_axis(b, g.ny, g.py);
-      int cw = c;
-      if (ok) ok = wrap_axis(cw, g.nz, g.pz);
-      if (ok) ok = !grid_solid(g, a, b, cw);
-      if (ok) {
-        const int64_t src = (a + g.hx) + g.sx * (int64_t)(b + g.hy) + g.sxy * ((int64_t)c + g.hz + p.zo_read);
-        d[i] = L.ld(i, src);
-      } else {
-        d[i] = L.ld(OPP(i), own_old);
-      }
-    }
-    T drho, rjx;
-    collide<T, FORCE>(d, T(p.omega), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
-    m += 1.0 + (double)drho;
-    jsum += (double)rjx;
-    const int64_t own_new = (x + g.hx) + g.sx * (int64_t)(y + g.hy) + g.sxy * ((int64_t)z + g.hz + p.zo_write);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) L.st(i, own_new, d[i]);
+  for (int i = 1; i < Q; ++i) {
+    const int src = nd.template nbf<FAST>(p, OPP(i));
+    d[i] = (FAST || src >= 0) ? A.ld(i, src) : A.ld(OPP(i), nd.s);
   }
-  if (RED) block_reduce_store(m, jsum, p.partials);
+  T drho, rjx;
+  collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+  m += 1.0 + (double)drho;
+  j += (double)rjx;
+  nd.launder_all();
+  const int64_t w = nd.s + shift;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) A.st(i, w, d[i]);
+}
+
+// Planes [z0, z1) of one sweep; the launch's grid covers (x, y) with 2D
+// blocks and grid z over the slab's planes.  p.g.zoff is the old offset
+// (plus the ghost plane), p.g.zghost is set on a periodic z axis.
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, C::kMinBlocks) k_cg_slab(StepParams p) {
+  Lattice<C, AOS> A{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
+  const int64_t shift = p.g.sxy * (int64_t)(p.zo_write - p.zo_read);
+  double m = 0.0, j = 0.0;
+  for (int z = p.z0 + blockIdx.z; z < p.z1; z += gridDim.z) {
+    DirectNode nd;
+    if (!nd.init_it(p, z)) continue;
+    if (nd.fast)
+      cg_node<true, C, AOS, FORCE>(p, nd, A, shift, m, j);
+    else
+      cg_node<false, C, AOS, FORCE>(p, nd, A, shift, m, j);
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
 }
 
 // Copy plane nz-1 to ghost plane -1 and plane 0 to ghost plane nz (offset zo),
@@ -85,7 +93,10 @@ __global__ void k_cg_ghost(S *A, int64_t npad, Grid g, int zo) {
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchCG {
   static void run(const StepParams &p, const LaunchShape &L) {
-    k_cg_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+    StepParams q = p;
+    q.g.zoff = p.zo_read;
+    q.g.zghost = p.g.pz;
+    k_cg_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
   }
 };
 
@@ -113,6 +124,143 @@ void launch_cg_ghost(const StepParams &p, int precision, int aos, int zo, cudaSt
     else
       k_cg_ghost<__half, 0><<<grid, 256, 0, s>>>(static_cast<__half *>(p.A), p.npad, p.g, zo);
   }
+}
+
+}  // namespace lbmk
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// Compressed grid on a node list.  The post-collision state of node n lives at
+// slot n + o + G, o alternating between 0 and K, G = nodes of the last plane
+// (room for the lower ghost copies).  Neighbour references are "unwrapped":
+// a link that wraps across the periodic z faces points at a ghost copy
+// (m - N below node 0, m + N above node N - 1) instead of node m, so every
+// link spans at most D node numbers.  A sweep reads at offset o and writes at
+// o'; writing slot n + o' overwrites the old data of position n + o' - o,
+// whose readers lie within D of it; with slabs of B consecutive nodes and
+// K >= D + B, descending slabs when o' > o and ascending slabs otherwise, all
+// of those readers are in earlier slabs.  Ghost copies are refreshed before
+// each sweep on a periodic z axis.
+
+constexpr int32_t kCgSolid = INT32_MIN;
+
+// Unwrapped index cidx[i-1][n] (kCgSolid for a solid/wall link), the largest
+// |u - n| (atomicMax into dmax), and the node counts of planes 0 and nz-1.
+__global__ void k_cg_ind_prep(const int32_t *idx, int64_t ipad, const int32_t *cells, int64_t N, int nx, int ny,
+                              int nz, int32_t *cidx, int *dmax, int *count_first, int *count_last) {
+  const int64_t plane = (int64_t)nx * ny;
+  int local_max = 0;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(cells[n] / plane);
+    if (z == 0) atomicAdd(count_first, 1);
+    if (z == nz - 1) atomicAdd(count_last, 1);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int32_t m = idx[(int64_t)(i - 1) * ipad + n];
+      int64_t u = m;
+      if (m < 0) {
+        cidx[(int64_t)(i - 1) * ipad + n] = kCgSolid;
+        continue;
+      }
+      if (CZ(i) < 0 && z == 0) u = (int64_t)m - N;
+      if (CZ(i) > 0 && z == nz - 1) u = (int64_t)m + N;
+      cidx[(int64_t)(i - 1) * ipad + n] = (int32_t)u;
+      const int64_t d = u > n ? u - n : n - u;
+      if (d > local_max) local_max = (int)d;
+    }
+  }
+  atomicMax(dmax, local_max);
+}
+
+void launch_cg_ind_prep(const int32_t *idx, int64_t ipad, const int32_t *cells, int64_t N, int nx, int ny, int nz,
+                        int32_t *cidx, int *counters, cudaStream_t s) {
+  if (N == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((N + 255) / 256, 1 << 16);
+  k_cg_ind_prep<<<grid, 256, 0, s>>>(idx, ipad, cells, N, nx, ny, nz, cidx, counters, counters + 1, counters + 2);
+}
+
+// Lower ghosts: copies of the last-plane nodes at positions m - N; upper
+// ghosts: copies of the first-plane nodes at m + N.  A points at position 0
+// of the current offset.
+template <class S, int AOS>
+__global__ void k_cg_ind_ghost(S *A, int64_t npad, int64_t N, int64_t nfirst, int64_t nlast) {
+  const int64_t per = nfirst + nlast;
+  const int64_t total = per * Q;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / per);
+    const int64_t r = t % per;
+    int64_t src, dst;
+    if (r < nlast) {
+      src = N - nlast + r;
+      dst = src - N;
+    } else {
+      src = r - nlast;
+      dst = src + N;
+    }
+    if (AOS)
+      A[dst * Q + i] = A[src * Q + i];
+    else
+      A[(int64_t)i * npad + dst] = A[(int64_t)i * npad + src];
+  }
+}
+
+void launch_cg_ind_ghost(void *A, int64_t npad, int precision, int aos, int64_t N, int64_t nfirst, int64_t nlast,
+                         cudaStream_t s) {
+  const int64_t total = (nfirst + nlast) * Q;
+  if (total == 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
+  if (precision == 0) {
+    if (aos) k_cg_ind_ghost<double, 1><<<grid, 256, 0, s>>>(static_cast<double *>(A), npad, N, nfirst, nlast);
+    else k_cg_ind_ghost<double, 0><<<grid, 256, 0, s>>>(static_cast<double *>(A), npad, N, nfirst, nlast);
+  } else if (precision == 1) {
+    if (aos) k_cg_ind_ghost<float, 1><<<grid, 256, 0, s>>>(static_cast<float *>(A), npad, N, nfirst, nlast);
+    else k_cg_ind_ghost<float, 0><<<grid, 256, 0, s>>>(static_cast<float *>(A), npad, N, nfirst, nlast);
+  } else {
+    if (aos) k_cg_ind_ghost<__half, 1><<<grid, 256, 0, s>>>(static_cast<__half *>(A), npad, N, nfirst, nlast);
+    else k_cg_ind_ghost<__half, 0><<<grid, 256, 0, s>>>(static_cast<__half *>(A), npad, N, nfirst, nlast);
+  }
+}
+
+// One slab [z0, z1) of node numbers (p.z0/p.z1 reused as node bounds): gather
+// from p.A (old offset) through the unwrapped index p.idx, collide, store to
+// p.B (new offset).
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, (step_min_cg<C>())) k_cg_ind_slab(StepParams p) {
+  using T = typename C::T;
+  Lattice<C, AOS> A{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
+  Lattice<C, AOS> B{static_cast<typename C::S *>(p.B), p.npad, p.scale, p.inv_scale};
+  double m = 0.0, j = 0.0;
+  for (int64_t n64 = p.slab0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n64 < p.slab1;
+       n64 += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)n64;
+    T d[Q];
+    d[0] = A.ld(0, n);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int32_t src = __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.ipad + n);
+      d[i] = src != kCgSolid ? A.ld(i, src) : A.ld(OPP(i), n);
+    }
+    T drho, rjx;
+    collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+    m += 1.0 + (double)drho;
+    j += (double)rjx;
+    const int w = launder(n);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) B.st(i, w, d[i]);
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+struct LaunchCGInd {
+  static void run(const StepParams &p, const LaunchShape &L) {
+    k_cg_ind_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+  }
+};
+
+void launch_cg_ind_slab(const StepParams &p, const KernelKey &k, const LaunchShape &L) {
+  dispatch<LaunchCGInd>(k.precision, k.aos, false, k.force, k.red, p, L);
 }
 
 }  // namespace lbmk

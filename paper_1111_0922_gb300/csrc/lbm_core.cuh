@@ -88,6 +88,8 @@ struct Grid {
   int64_t sx, sxy;
   int64_t zoff;
   const uint8_t *solid;  // per cell, or nullptr when every cell is fluid
+  int zghost;            // periodic z through ghost planes (compressed grid):
+                         // z deltas stay +-1, only the solid lookup wraps
 };
 
 __device__ __forceinline__ int64_t grid_slot(const Grid &g, int x, int y, int z) {
@@ -131,16 +133,20 @@ __device__ __forceinline__ int64_t grid_position(const Grid &g, int x, int y, in
 }
 
 // ---------------------------------------------------------------------------
-// BGK collision with the Guo forcing term, in shifted variables.
+// Collision with the Guo forcing term, in shifted variables: two-relaxation-
+// time (TRT) with rates lp (symmetric halves, sets the viscosity) and lm
+// (antisymmetric halves); lm = lp is BGK.
 //   d_i = f_i - w_i,  rho = 1 + sum d_i,  j = sum c_i d_i  (sum c_i w_i = 0)
 //   u = (j + rho g / 2) / rho
-//   d_eq,i = w_i [ (rho - 1) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u) ]
-//   F_i    = (1 - omega/2) w_i rho [ 3 (c_i - u).g + 9 (c_i.u)(c_i.g) ]
-//   d*_i   = d_i - omega (d_i - d_eq,i) + F_i
-// Opposite pairs share c.u up to sign, which the pair loop exploits.
+//   for an opposite pair (i, opp i), with a = (d_i + d_opp)/2, b = (d_i - d_opp)/2:
+//     a_eq = w_i [ (rho - 1) + rho (4.5 (c.u)^2 - 1.5 u.u) ],  b_eq = w_i 3 rho c.u
+//     F+ = (1 - lp/2) w_i rho (9 (c.u)(c.g) - 3 u.g),  F- = (1 - lm/2) w_i rho 3 c.g
+//     a* = a - lp (a - a_eq) + F+,  b* = b - lm (b - b_eq) + F-
+//     d*_i = a* + b*,  d*_opp = a* - b*
+//   rest: d*_0 = d_0 - lp (d_0 - w_0 [(rho - 1) - 1.5 rho u.u]) - (1 - lp/2) w_0 rho 3 u.g
 // Returns rho - 1 and rho u_x (for the mass and flux reductions).
 template <typename T, bool FORCE>
-__device__ __forceinline__ void collide(T (&d)[Q], T omega, T gx, T gy, T gz, T &drho_out, T &rjx_out) {
+__device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz, T &drho_out, T &rjx_out) {
   T sum[10], dif[10];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
@@ -176,15 +182,14 @@ __device__ __forceinline__ void collide(T (&d)[Q], T omega, T gx, T gy, T gz, T 
   drho_out = drho;
   rjx_out = rho * ux;
   const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-  const T om1 = T(1) - omega;
-  const T kf = T(1) - T(0.5) * omega;
+  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);  // (1 - l)/2: a = sum/2, b = dif/2
+  const T kp = T(1) - T(0.5) * lp, km = T(1) - T(0.5) * lm;
   T ug = 0;
   if (FORCE) ug = ux * gx + uy * gy + uz * gz;
   {
     const T w = T(WD(0));
-    T deq = w * (drho - rho * usq15);
-    T v = om1 * d[0] + omega * deq;
-    if (FORCE) v -= kf * w * rho * T(3) * ug;
+    T v = (T(1) - lp) * d[0] + lp * w * (drho - rho * usq15);
+    if (FORCE) v -= kp * w * rho * T(3) * ug;
     d[0] = v;
   }
 #pragma unroll
@@ -195,18 +200,16 @@ __device__ __forceinline__ void collide(T (&d)[Q], T omega, T gx, T gy, T gz, T 
     if (CX(i)) { cu += T(CX(i)) * ux; if (FORCE) cg += T(CX(i)) * gx; }
     if (CY(i)) { cu += T(CY(i)) * uy; if (FORCE) cg += T(CY(i)) * gy; }
     if (CZ(i)) { cu += T(CZ(i)) * uz; if (FORCE) cg += T(CZ(i)) * gz; }
-    const T sym = drho + rho * (T(4.5) * cu * cu - usq15);
-    const T asym = T(3) * rho * cu;
-    T vp = om1 * d[i] + omega * w * (sym + asym);
-    T vm = om1 * d[i + 1] + omega * w * (sym - asym);
+    const T aeq = drho + rho * (T(4.5) * cu * cu - usq15);
+    const T beq = T(3) * rho * cu;
+    T a = hp * sum[k] + lp * w * aeq;
+    T b = hm * dif[k] + lm * w * beq;
     if (FORCE) {
-      const T fs = kf * w * rho * (T(9) * cu * cg - T(3) * ug);
-      const T fa = kf * w * rho * T(3) * cg;
-      vp += fs + fa;
-      vm += fs - fa;
+      a += kp * w * rho * (T(9) * cu * cg - T(3) * ug);
+      b += km * w * rho * T(3) * cg;
     }
-    d[i] = vp;
-    d[i + 1] = vm;
+    d[i] = a + b;
+    d[i + 1] = a - b;
   }
 }
 
@@ -224,11 +227,13 @@ struct StepParams {
   int64_t ipad;
   int map[Q];         // esoteric twist: physical array of direction i
   double omega, gx, gy, gz;
+  double omega_m;     // antisymmetric rate (TRT); equal to omega for BGK
   float scale, inv_scale;
   double *partials;   // fused reduction: 2 doubles per block, or nullptr
   int *err;           // device error word
   int z0, z1;         // compressed grid: planes of this launch
   int zo_read, zo_write;  // compressed grid: plane offsets of the old and new state
+  int64_t slab0, slab1;   // compressed grid on a node list: node numbers of this launch
 };
 
 // Hide a value's provenance from the optimiser: addresses derived from the
@@ -251,6 +256,7 @@ struct DirectNode {
   int s;      // own storage slot
   int cell;   // own cell (solid mask index)
   int dx[2], dy[2], dz[2];
+  int dzc[2];     // z deltas for the solid lookup (wrapped even with ghost planes)
   unsigned wall;  // bit 2a + side: face (axis a, -1 / +1 side) is a wall
   bool fast;      // no wall face and no solid mask: every neighbour is fluid
 
@@ -271,6 +277,12 @@ struct DirectNode {
     if (y == g.ny - 1) { if (g.py) dy[1] = 1 - g.ny; else wall |= 8u; }
     if (z == 0) { if (g.pz) dz[0] = g.nz - 1; else wall |= 16u; }
     if (z == g.nz - 1) { if (g.pz) dz[1] = 1 - g.nz; else wall |= 32u; }
+    dzc[0] = dz[0];
+    dzc[1] = dz[1];
+    if (g.zghost) {
+      dz[0] = -1;
+      dz[1] = 1;
+    }
     fast = wall == 0 && g.solid == nullptr;
     return true;
   }
@@ -303,6 +315,8 @@ struct DirectNode {
     dy[1] = launder(dy[1]);
     dz[0] = launder(dz[0]);
     dz[1] = launder(dz[1]);
+    dzc[0] = launder(dzc[0]);
+    dzc[1] = launder(dzc[1]);
     wall = (unsigned)launder((int)wall);
     fast = launder((int)fast) != 0;
   }
@@ -328,7 +342,8 @@ struct DirectNode {
     const int ex = CX(i) < 0 ? dx[0] : (CX(i) > 0 ? dx[1] : 0);
     const int ey = CY(i) < 0 ? dy[0] : (CY(i) > 0 ? dy[1] : 0);
     const int ez = CZ(i) < 0 ? dz[0] : (CZ(i) > 0 ? dz[1] : 0);
-    if (p.g.solid && p.g.solid[cell + ex + p.g.nx * (ey + p.g.ny * ez)]) return -1;
+    const int ec = CZ(i) < 0 ? dzc[0] : (CZ(i) > 0 ? dzc[1] : 0);
+    if (p.g.solid && p.g.solid[cell + ex + p.g.nx * (ey + p.g.ny * ec)]) return -1;
     return s + ex + (int)p.g.sx * ey + (int)p.g.sxy * ez;
   }
 };

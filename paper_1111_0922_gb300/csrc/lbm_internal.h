@@ -54,6 +54,12 @@ inline void launch_step_kernel_cg(const StepParams &p, const KernelKey &k, const
   launch_cg_slab(p, k, L);
 }
 void launch_cg_ghost(const StepParams &p, int precision, int aos, int zo, cudaStream_t s);
+// node lists: unwrapped index + counters {D, nodes in plane 0, nodes in plane nz-1}
+void launch_cg_ind_prep(const int32_t *idx, int64_t ipad, const int32_t *cells, int64_t N, int nx, int ny, int nz,
+                        int32_t *cidx, int *counters, cudaStream_t s);
+void launch_cg_ind_ghost(void *A, int64_t npad, int precision, int aos, int64_t N, int64_t nfirst, int64_t nlast,
+                         cudaStream_t s);
+void launch_cg_ind_slab(const StepParams &p, const KernelKey &k, const LaunchShape &L);
 
 // lbm_swap.cu: one colour pass of the blocked swap
 struct SwapTiles {
@@ -65,6 +71,8 @@ struct SwapTiles {
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
 size_t swap_smem_bytes(const SwapTiles &t, int precision);
 int swap_colours(const SwapTiles &t, int px, int py, int pz);
+// node lists: link exchanges after a collide-into-reversed-slots pass
+void launch_swap_links(const StepParams &p, int precision, int aos, cudaStream_t s);
 int swap_blocks(const SwapTiles &t, int px, int py, int pz, int colour);
 
 // lbm_setup.cu

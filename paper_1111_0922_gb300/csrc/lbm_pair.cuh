@@ -73,8 +73,8 @@ __device__ __forceinline__ void pair_collide(typename C::T (&d0)[Q], typename C:
                                              double &m, double &j) {
   using T = typename C::T;
   T r0, j0, r1, j1;
-  collide<T, FORCE>(d0, T(p.omega), T(p.gx), T(p.gy), T(p.gz), r0, j0);
-  collide<T, FORCE>(d1, T(p.omega), T(p.gx), T(p.gy), T(p.gz), r1, j1);
+  collide<T, FORCE>(d0, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), r0, j0);
+  collide<T, FORCE>(d1, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), r1, j1);
   m += 2.0 + (double)r0 + (double)r1;
   j += (double)j0 + (double)j1;
 }

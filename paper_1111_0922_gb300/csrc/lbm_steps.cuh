@@ -46,7 +46,7 @@ using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
 template <typename T, bool FORCE>
 __device__ __forceinline__ void run_collision(T (&d)[Q], const StepParams &p, double &m, double &j) {
   T drho, rjx;
-  collide<T, FORCE>(d, T(p.omega), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+  collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
   m += 1.0 + (double)drho;
   j += (double)rjx;
 }
@@ -79,6 +79,17 @@ __global__ void LBM_STEP_BOUNDS k_ts_collide(StepParams p) {
 
 // Two-step, kernel 2 (Tab. 1, propagation), pull form: A_i(x) = B_i(x - c_i),
 // or B_opp(i)(x) across a solid/wall link.  Raw copies: bit-exact.
+template <bool FAST, class C, int AOS, class Node>
+__device__ __forceinline__ void ts_stream_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
+                                               const Lattice<C, AOS> &B) {
+  *A.at(0, nd.s) = *B.at(0, nd.s);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int src = nd.template nbf<FAST>(p, OPP(i));
+    *A.at(i, nd.s) = (FAST || src >= 0) ? *B.at(i, src) : *B.at(OPP(i), nd.s);
+  }
+}
+
 template <class C, int AOS, class Node>
 __global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
   const auto A = lattice_of<C, AOS>(p.A, p);
@@ -86,12 +97,10 @@ __global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    *A.at(0, nd.s) = *B.at(0, nd.s);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int src = nd.nb(p, OPP(i));
-      *A.at(i, nd.s) = src >= 0 ? *B.at(i, src) : *B.at(OPP(i), nd.s);
-    }
+    if (nd.fast)
+      ts_stream_node<true, C, AOS, Node>(p, nd, A, B);
+    else
+      ts_stream_node<false, C, AOS, Node>(p, nd, A, B);
   }
 }
 

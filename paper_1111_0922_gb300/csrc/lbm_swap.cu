@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = L.ld(i, s);
     T drho, rjx;
-    collide<T, FORCE>(d, T(p.omega), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+    collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
     m = 1.0 + (double)drho;
     jsum = (double)rjx;
 #pragma unroll
@@ -187,6 +187,50 @@ int swap_blocks(const SwapTiles &t, int px, int py, int pz, int colour) {
   axis_set(t.nty, py, (colour / cx) % cy, st, c1);
   axis_set(t.ntz, pz, colour / (cx * cy), st, c2);
   return c0 * c1 * c2;
+}
+
+}  // namespace lbmk
+
+namespace lbmk {
+
+// Swap on a node list (Sec. 5, Tab. 4), order-free form.  After the nodes
+// have been collided into their reversed slots (the AA pattern's even kernel:
+// the post-collision PDF along c_i sits in the node's slot of the opposite
+// direction), every link is completed by exchanging the two PDFs that travel
+// along it.  Thread n owns the links to its neighbours along the nine odd
+// directions: it exchanges slot opp(i) of n with slot i of IDX[i][n].  Local
+// slots (even directions) and remote slots (odd directions) are disjoint and
+// each link has one owner, so the exchanges need no ordering; a solid or wall
+// link needs none (its reversed slot already holds the bounced-back PDF).
+template <class S, int AOS>
+__global__ void __launch_bounds__(256) k_swap_links(S *A, int64_t npad, const int32_t *idx, int64_t ipad,
+                                                    int64_t nnodes) {
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int m = __ldg(idx + (int64_t)(i - 1) * ipad + n);
+      if (m < 0) continue;
+      S *a = AOS ? A + n * Q + OPP(i) : A + (int64_t)OPP(i) * npad + n;
+      S *b = AOS ? A + (int64_t)m * Q + i : A + (int64_t)i * npad + m;
+      const S t = *a;
+      *a = *b;
+      *b = t;
+    }
+  }
+}
+
+void launch_swap_links(const StepParams &p, int precision, int aos, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p.nnodes + 255) / 256, 1 << 20));
+  if (precision == 0) {
+    if (aos) k_swap_links<double, 1><<<grid, 256, 0, s>>>(static_cast<double *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+    else k_swap_links<double, 0><<<grid, 256, 0, s>>>(static_cast<double *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+  } else if (precision == 1) {
+    if (aos) k_swap_links<float, 1><<<grid, 256, 0, s>>>(static_cast<float *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+    else k_swap_links<float, 0><<<grid, 256, 0, s>>>(static_cast<float *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+  } else {
+    if (aos) k_swap_links<__half, 1><<<grid, 256, 0, s>>>(static_cast<__half *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+    else k_swap_links<__half, 0><<<grid, 256, 0, s>>>(static_cast<__half *>(p.A), p.npad, p.idx, p.ipad, p.nnodes);
+  }
 }
 
 }  // namespace lbmk

@@ -42,7 +42,7 @@ class lbm_config(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("addressing", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("force", ctypes.c_double * 3),
-                ("f16_scale", ctypes.c_double),
+                ("f16_scale", ctypes.c_double), ("trt_magic", ctypes.c_double),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("cg_shift", ctypes.c_int32), ("pair_x", ctypes.c_int32),
                 ("stream", ctypes.c_void_p),
@@ -319,7 +319,7 @@ class Lattice:
     def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
                  layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
                  f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0, pair_x=0,
-                 stream=None, use_torch_allocator=True):
+                 trt_magic=0.0, stream=None, use_torch_allocator=True):
         self.cfg = lbm_config_default()
         c = self.cfg
         c.nx, c.ny, c.nz = (int(d) for d in dims)
@@ -333,6 +333,7 @@ class Lattice:
         c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         c.omega = float(omega)
         c.f16_scale = float(f16_scale)
+        c.trt_magic = float(trt_magic)
         c.block_size = int(block_size)
         c.nodes_per_thread = int(nodes_per_thread)
         c.cg_shift = int(cg_shift)

@@ -72,7 +72,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--nodes-per-thread", type=int, default=0)
-    ap.add_argument("--pair-x", type=int, default=0, help="AA on a full grid: 0 = x pairs where possible, 1 = off")
+    ap.add_argument("--pair-x", type=int, default=0, help="AA on a full grid: 1 = two x-adjacent nodes per thread")
     args = ap.parse_args(argv)
     import torch
 

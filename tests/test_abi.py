@@ -42,8 +42,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes(lib):
     from paper_1111_0922_gb300 import lbm
 
-    # 3+3+4 int32, 5 doubles, 4 int32, 4 pointers
-    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 5 * 8 + 4 * 4 + 4 * 8
+    # 3+3+4 int32, 6 doubles, 4 int32, 4 pointers
+    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 4 * 4 + 4 * 8
     assert ctypes.sizeof(lbm.lbm_info) == 6 * 8 + 2 * 4 + 8 + 2 * 4
 
 
