@@ -338,6 +338,65 @@ def run_sparse(torch, lbm, args, hbm):
     return out
 
 
+def run_sparse_solve(torch, lbm, args):
+    """The 512^3 pack run to a steady flux (relative change < 1e-6 between
+    rounds of 100 steps), AA pattern on the node list, FP32 and FP16 storage."""
+    from paper_1111_0922_gb300 import permeability
+
+    dims = (512, 512, 512)
+    pack = inputs.sphere_pack(dims, 0.6, radius=8.0, seed=SEED + 1)
+    out = {}
+    for precision in ("f32", "f16s"):
+        lat = lbm.Lattice(dims, (1, 1, 1), variant="aa", addressing="indirect", precision=precision, omega=1.0,
+                          force=(1e-6, 0.0, 0.0))
+        lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
+        lat.init()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = permeability.solve(lat, 1.0, 1e-6, max_steps=args.solve_max_steps)
+        secs = time.perf_counter() - t0
+        n = int(lat.info.nodes)
+        out[precision] = {"k": res.k, "steps": res.steps, "converged": res.converged, "seconds": round(secs, 2),
+                          "mflups": round(n * res.steps / secs / 1e6, 1), "f16_scale": lat.info.f16_scale}
+        lat.close()
+        torch.cuda.empty_cache()
+        log("solve", precision, out[precision])
+    if out["f32"]["converged"] and out["f16s"]["converged"]:
+        out["k_rel_diff_f16s_vs_f32"] = abs(out["f16s"]["k"] - out["f32"]["k"]) / out["f32"]["k"]
+    return out
+
+
+def run_paper_shapes(torch, lbm, args, hbm):
+    """The paper's benchmark geometries (Sec. 10): the 500x100x100 empty
+    channel and a packed bed of spheres with about 2.1 M fluid cells, flow
+    along x, walls on y/z; node-list addressing, SoA, TRT (magic 3/16) as the
+    paper's solver, FP64 and FP32."""
+    out = {}
+    shapes = {"channel": (inputs.paper_channel(), None), "bed": (None, inputs.paper_packed_bed())}
+    for name, (chan, pack) in shapes.items():
+        for variant in ("os_push", "os_pull", "aa", "et"):
+            for precision in ("f64", "f32"):
+                dims, per = chan if chan else (pack.dims, pack.periodic)
+                lat = lbm.Lattice(dims, per, variant=variant, addressing="indirect", precision=precision,
+                                  omega=1.0, force=(1e-6, 0.0, 0.0), trt_magic=3.0 / 16.0)
+                if pack is None:
+                    lat.set_geometry(None)
+                else:
+                    lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
+                lat.init()
+                lat.step(4)
+                total, _ = timed_steps(torch, lat, args.shape_steps, per_launch=False)
+                n = int(lat.info.nodes)
+                mflups = n * args.shape_steps / total / 1e6
+                roof = model.roof_mflups(variant, True, precision, hbm)
+                out["%s/%s/%s" % (name, variant, precision)] = {
+                    "fluid_nodes": n, "mflups": round(mflups, 1), "frac_of_hbm_roof": round(mflups / roof, 4)}
+                lat.close()
+                torch.cuda.empty_cache()
+    log("paper_shapes", out)
+    return out
+
+
 def run_batch(torch, lbm, args):
     """64 sphere packs, cube sides U{32..192}, porosity U[0.3, 0.8), r = 8
     (seed 4); FP32 AA pattern on concatenated node lists, launch shape from the
@@ -482,6 +541,10 @@ def main_gb300(args):
         result["variants"] = run_sweep(torch, lbm, args, hbm)
     if rank == 0 and not args.no_sparse:
         result["sparse"] = run_sparse(torch, lbm, args, hbm)
+        if not args.no_solve:
+            result["sparse"]["steady_flux"] = run_sparse_solve(torch, lbm, args)
+    if rank == 0 and not args.no_shapes:
+        result["paper_shapes"] = run_paper_shapes(torch, lbm, args, hbm)
     if rank == 0 and not args.no_batch:
         result["batch"] = run_batch(torch, lbm, args)
         log("batch", result["batch"])
@@ -546,6 +609,10 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--sparse-steps", type=int, default=50)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-max-steps", type=int, default=20000)
+    ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--shape-steps", type=int, default=50)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-seconds", type=float, default=60.0)

@@ -97,7 +97,8 @@ typedef struct lbm_config {
                                 half-way for Poiseuille flow) */
   int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128 */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default */
-  int32_t cg_shift;          /* LBM_CG: shift k in planes (direct) >= 2; 0 = default */
+  int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes);
+                                node list: slab size B >= 1 nodes; 0 = default */
   int32_t pair_x;            /* LBM_AA, full grid, SoA: 1 = two x-adjacent nodes per thread with vector
                                 accesses where possible (periodic x, even nx, no solid cell);
                                 0 = one node per thread (default, faster on GB300) */

@@ -252,7 +252,7 @@ static SwapTiles swap_tiles(const lbm_t *h) {
   SwapTiles t;
   t.tx = std::min(32, h->cfg.nx);
   t.ty = std::min(4, h->cfg.ny);
-  t.tz = std::min(4, h->cfg.nz);
+  t.tz = std::min(2, h->cfg.nz);
   t.ntx = (h->cfg.nx + t.tx - 1) / t.tx;
   t.nty = (h->cfg.ny + t.ty - 1) / t.ty;
   t.ntz = (h->cfg.nz + t.tz - 1) / t.tz;
@@ -335,7 +335,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
     if (std::frexp(cfg->f16_scale, &e) != 0.5) return fail(nullptr, LBM_ERR_INVALID_ARG, "f16_scale must be 2^k");
   }
   if (cfg->dev_alloc && !cfg->dev_free) return fail(nullptr, LBM_ERR_INVALID_ARG, "dev_alloc without dev_free");
-  if (cfg->cg_shift != 0 && cfg->cg_shift < 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift must be >= 2");
+  if (cfg->cg_shift < 0 || (cfg->addressing == LBM_DIRECT && cfg->cg_shift == 1))
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift: >= 2 planes on a full grid, >= 1 node on a node list");
   if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
 
   lbm_t *h = new lbm_t();

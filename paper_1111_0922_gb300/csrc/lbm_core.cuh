@@ -182,8 +182,7 @@ __device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz,
   drho_out = drho;
   rjx_out = rho * ux;
   const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);  // (1 - l)/2: a = sum/2, b = dif/2
-  const T kp = T(1) - T(0.5) * lp, km = T(1) - T(0.5) * lm;
+  const T kp = T(1) - T(0.5) * lp;
   T ug = 0;
   if (FORCE) ug = ux * gx + uy * gy + uz * gz;
   {
@@ -192,6 +191,34 @@ __device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz,
     if (FORCE) v -= kp * w * rho * T(3) * ug;
     d[0] = v;
   }
+  if (lm == lp) {
+    // BGK: d*_i = (1 - omega) d_i + omega d_eq,i (+ F_i), per pair
+    const T om1 = T(1) - lp;
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      const int i = 2 * k - 1;
+      const T w = T(WD(i));
+      T cu = 0, cg = 0;
+      if (CX(i)) { cu += T(CX(i)) * ux; if (FORCE) cg += T(CX(i)) * gx; }
+      if (CY(i)) { cu += T(CY(i)) * uy; if (FORCE) cg += T(CY(i)) * gy; }
+      if (CZ(i)) { cu += T(CZ(i)) * uz; if (FORCE) cg += T(CZ(i)) * gz; }
+      const T sym = drho + rho * (T(4.5) * cu * cu - usq15);
+      const T asym = T(3) * rho * cu;
+      T vp = om1 * d[i] + lp * w * (sym + asym);
+      T vm = om1 * d[i + 1] + lp * w * (sym - asym);
+      if (FORCE) {
+        const T fs = kp * w * rho * (T(9) * cu * cg - T(3) * ug);
+        const T fa = kp * w * rho * T(3) * cg;
+        vp += fs + fa;
+        vm += fs - fa;
+      }
+      d[i] = vp;
+      d[i + 1] = vm;
+    }
+    return;
+  }
+  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);  // (1 - l)/2: a = sum/2, b = dif/2
+  const T km = T(1) - T(0.5) * lm;
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;

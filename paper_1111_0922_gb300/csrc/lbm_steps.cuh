@@ -79,15 +79,21 @@ __global__ void LBM_STEP_BOUNDS k_ts_collide(StepParams p) {
 
 // Two-step, kernel 2 (Tab. 1, propagation), pull form: A_i(x) = B_i(x - c_i),
 // or B_opp(i)(x) across a solid/wall link.  Raw copies: bit-exact.
+// All 19 values are loaded before any store: a store to A might alias a later
+// load from B as far as the compiler knows, which would serialise the copies.
 template <bool FAST, class C, int AOS, class Node>
 __device__ __forceinline__ void ts_stream_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
                                                const Lattice<C, AOS> &B) {
-  *A.at(0, nd.s) = *B.at(0, nd.s);
+  typename C::S v[Q];
+  v[0] = *B.at(0, nd.s);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int src = nd.template nbf<FAST>(p, OPP(i));
-    *A.at(i, nd.s) = (FAST || src >= 0) ? *B.at(i, src) : *B.at(OPP(i), nd.s);
+    v[i] = (FAST || src >= 0) ? *B.at(i, src) : *B.at(OPP(i), nd.s);
   }
+  nd.launder_all();
+#pragma unroll
+  for (int i = 0; i < Q; ++i) *A.at(i, nd.s) = v[i];
 }
 
 template <class C, int AOS, class Node>

@@ -36,28 +36,70 @@ __device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
   return t & 1;
 }
 
+// Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
+__host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
+
+// One pass: the tiles of one colour.  Thread (lx, ly, lz) of the block owns
+// cell org + (lx, ly, lz) of its tile.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
+__global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp) {
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);
+  __shared__ unsigned earlier_mask, self_mask;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const Grid &g = p.g;
   const int TN = sp.tx * sp.ty * sp.tz;
-  // which tile of this colour
-  const int kx = blockIdx.x, ky = blockIdx.y, kz = blockIdx.z;
-  const int tile[3] = {sp.start[0] + 2 * kx, sp.start[1] + 2 * ky, sp.start[2] + 2 * kz};
+  const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
+                       sp.start[2] + 2 * (int)blockIdx.z};
   const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
   const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (t == 0) {
+    // classify the 26 neighbouring tiles once per block
+    const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
+    const int per[3] = {g.px, g.py, g.pz};
+    unsigned em = 0, sm = 0;
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          const int o[3] = {ox, oy, oz};
+          int nb[3];
+          bool exists = true;
+          for (int a = 0; a < 3; ++a) {
+            nb[a] = tile[a] + o[a];
+            if (nb[a] < 0 || nb[a] >= nt[a]) {
+              if (!per[a]) exists = false;
+              nb[a] = (nb[a] + nt[a]) % nt[a];
+            }
+          }
+          if (!exists) continue;
+          if (nb[0] == tile[0] && nb[1] == tile[1] && nb[2] == tile[2]) {
+            sm |= 1u << tile_bit(ox, oy, oz);
+            continue;
+          }
+          const int col = axis_colour(nb[0], nt[0], per[0]) +
+                          sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
+          if (col < sp.colour) em |= 1u << tile_bit(ox, oy, oz);
+        }
+    earlier_mask = em;
+    self_mask = sm;
+  }
   const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
-  const int x = org[0] + lx, y = org[1] + ly, z = org[2] + lz;
-  const bool active = t < TN && x < g.nx && y < g.ny && z < g.nz && !grid_solid(g, x, y, z);
-  const int64_t s = active ? grid_slot(g, x, y, z) : 0;
+  // extent of this tile inside the box (the last tile of an axis may be cut)
+  const int ex = min(sp.tx, g.nx - org[0]), ey = min(sp.ty, g.ny - org[1]), ez = min(sp.tz, g.nz - org[2]);
+  DirectNode nd;
+  bool active = lx < ex && ly < ey && lz < ez;
+  if (active) {
+    nd.x = org[0] + lx;
+    nd.y = org[1] + ly;
+    nd.z = org[2] + lz;
+    active = nd.setup(g);
+  }
   double m = 0.0, jsum = 0.0;
   if (active) {
     T d[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = L.ld(i, s);
+    for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
     T drho, rjx;
     collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
     m = 1.0 + (double)drho;
@@ -67,53 +109,50 @@ __global__ void __launch_bounds__(512) k_swap_pass(StepParams p, SwapPass sp) {
   }
   __syncthreads();
   if (active) {
-    L.st(0, s, S[t]);
+    // Gather every incoming value first (the loads from earlier tiles are
+    // independent and overlap), then write: the remote slots written below
+    // belong to earlier tiles and are never read by this pass again.
+    const unsigned em = earlier_mask, sm = self_mask;
+    T v[Q];
+    int remote[Q];
+    v[0] = S[t];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      // the PDF arriving along c_i comes from y = x - c_i
-      int a = x - CX(i), bb = y - CY(i), c = z - CZ(i);
-      const bool linked = wrap_axis(a, g.nx, g.px) && wrap_axis(bb, g.ny, g.py) && wrap_axis(c, g.nz, g.pz) &&
-                          !grid_solid(g, a, bb, c);
-      T v;
-      if (!linked) {
-        v = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
-      } else {
-        // tile of the source cell along each axis, by comparison with this
-        // tile's bounds (no division): same, previous or next (wrapping)
-        const int src[3] = {a, bb, c};
-        const int d[3] = {-CX(i), -CY(i), -CZ(i)};
-        const int ext[3] = {sp.tx, sp.ty, sp.tz};
-        const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
-        const int per[3] = {g.px, g.py, g.pz};
-        int nt_idx[3];
-        bool same = true;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          if (src[ax] >= org[ax] && src[ax] < org[ax] + ext[ax]) {
-            nt_idx[ax] = tile[ax];
-          } else {
-            same = false;
-            nt_idx[ax] = d[ax] < 0 ? (tile[ax] == 0 ? nt[ax] - 1 : tile[ax] - 1)
-                                   : (tile[ax] == nt[ax] - 1 ? 0 : tile[ax] + 1);
-          }
-        }
-        if (same) {
-          const int u = (a - org[0]) + sp.tx * ((bb - org[1]) + sp.ty * (c - org[2]));
-          v = S[i * TN + u];
-        } else {
-          const int col = axis_colour(nt_idx[0], nt[0], per[0]) +
-                          sp.cx * (axis_colour(nt_idx[1], nt[1], per[1]) + sp.cy * axis_colour(nt_idx[2], nt[2], per[2]));
-          if (col < sp.colour) {
-            // earlier tile: its reversed slot holds the PDF for us; give it ours
-            const int64_t ys = grid_slot(g, a, bb, c);
-            v = L.ld(OPP(i), ys);
-            L.st(OPP(i), ys, S[OPP(i) * TN + t]);
-          } else {
-            v = S[OPP(i) * TN + t];  // later tile completes the link
-          }
-        }
+      remote[i] = -1;
+      // the PDF arriving along c_i comes from x - c_i
+      const int dx = -CX(i), dy = -CY(i), dz = -CZ(i);
+      const bool in_x = dx == 0 || (dx < 0 ? lx > 0 : lx < ex - 1);
+      const bool in_y = dy == 0 || (dy < 0 ? ly > 0 : ly < ey - 1);
+      const bool in_z = dz == 0 || (dz < 0 ? lz > 0 : lz < ez - 1);
+      if (in_x && in_y && in_z) {
+        v[i] = S[i * TN + t + dx + sp.tx * (dy + sp.ty * dz)];  // inside the tile
+        continue;
       }
-      L.st(i, s, v);
+      const int src = nd.nb(p, OPP(i));
+      if (src < 0) {
+        v[i] = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
+        continue;
+      }
+      const int bit = tile_bit(in_x ? 0 : dx, in_y ? 0 : dy, in_z ? 0 : dz);
+      if (sm & (1u << bit)) {
+        // the tile is its own neighbour across a periodic face
+        const int wx = in_x ? lx + dx : (dx < 0 ? ex - 1 : 0);
+        const int wy = in_y ? ly + dy : (dy < 0 ? ey - 1 : 0);
+        const int wz = in_z ? lz + dz : (dz < 0 ? ez - 1 : 0);
+        v[i] = S[i * TN + wx + sp.tx * (wy + sp.ty * wz)];
+      } else if (em & (1u << bit)) {
+        // earlier tile: its reversed slot holds the PDF for us; ours goes there
+        remote[i] = src;
+        v[i] = L.ld(OPP(i), src);
+      } else {
+        v[i] = S[OPP(i) * TN + t];  // a later tile completes the link
+      }
+    }
+    nd.launder_all();
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      L.st(i, nd.s, v[i]);
+      if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
     }
   }
   if (RED) block_reduce_store(m, jsum, p.partials);
@@ -128,6 +167,7 @@ struct LaunchSwap {
   }
 };
 
+// tiles are at most 32 x 4 x 2 = 256 cells (one thread each)
 size_t swap_smem_bytes(const SwapTiles &t, int precision) {
   return (size_t)Q * t.tx * t.ty * t.tz * (precision == 0 ? 8 : 4);
 }
@@ -206,15 +246,21 @@ template <class S, int AOS>
 __global__ void __launch_bounds__(256) k_swap_links(S *A, int64_t npad, const int32_t *idx, int64_t ipad,
                                                     int64_t nnodes) {
   for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += (int64_t)gridDim.x * blockDim.x) {
+    // load every value of the nine links, then store (no load waits on a store)
+    int m[Q];
+    S va[Q], vb[Q];
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
-      const int m = __ldg(idx + (int64_t)(i - 1) * ipad + n);
-      if (m < 0) continue;
-      S *a = AOS ? A + n * Q + OPP(i) : A + (int64_t)OPP(i) * npad + n;
-      S *b = AOS ? A + (int64_t)m * Q + i : A + (int64_t)i * npad + m;
-      const S t = *a;
-      *a = *b;
-      *b = t;
+      m[i] = __ldg(idx + (int64_t)(i - 1) * ipad + n);
+      if (m[i] < 0) continue;
+      va[i] = AOS ? A[n * Q + OPP(i)] : A[(int64_t)OPP(i) * npad + n];
+      vb[i] = AOS ? A[(int64_t)m[i] * Q + i] : A[(int64_t)i * npad + m[i]];
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      if (m[i] < 0) continue;
+      (AOS ? A[n * Q + OPP(i)] : A[(int64_t)OPP(i) * npad + n]) = vb[i];
+      (AOS ? A[(int64_t)m[i] * Q + i] : A[(int64_t)i * npad + m[i]]) = va[i];
     }
   }
 }

@@ -103,6 +103,21 @@ def sphere_pack(dims, porosity: float, radius: float = 8.0, seed: int = 3,
                       int(round(radius * unit)), int(unit), float(porosity))
 
 
+def paper_channel():
+    """The empty channel of the paper's benchmarks (Sec. 10): 500 x 100 x 100
+    cells, flow along x (periodic), bounce-back walls on the y and z faces;
+    every cell is fluid (5.0 M)."""
+    return (500, 100, 100), (1, 0, 0)
+
+
+def paper_packed_bed(seed: int = 6, radius: float = 6.0, porosity: float = 0.42) -> SpherePack:
+    """A packed bed of spheres in the paper's 500 x 100 x 100 box (Sec. 10,
+    Fig. 7): overlapping spheres of radius 6 cells, porosity 0.42 so that the
+    fluid cells number about 2.1 M as in the paper; periodic along the flow
+    axis x, walls on the y and z faces."""
+    return sphere_pack((500, 100, 100), porosity, radius, seed=seed, periodic=(1, 0, 0))
+
+
 def duct(n: int = 32):
     """The 32^3 duct: periodic along x, bounce-back walls on the y and z faces."""
     return (n, n, n), (1, 0, 0)

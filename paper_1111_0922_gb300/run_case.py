@@ -8,6 +8,8 @@ Workloads:
   pack<N>    periodic N^3 sphere pack, r = 8, porosity 0.6 (seed 3),
              g = 1e-6 along x, omega 1.0, from rest
   duct<N>    N^3 duct, periodic x, walls y/z, g = 1e-6 x, omega 1.0
+  channel    the paper's 500x100x100 empty channel (walls y/z), g = 1e-6 x
+  bed        the paper-shaped 500x100x100 packed bed (about 2.1 M fluid cells)
 Prints one JSON line: nodes, steps, seconds, MFLUP/s, bytes per FLUP, roof.
 """
 from __future__ import annotations
@@ -39,7 +41,8 @@ def setup(args):
     dims = (size, size, size)
     common = dict(variant=args.variant, addressing=args.addressing, layout=args.layout,
                   precision=args.precision, block_size=args.block_size,
-                  nodes_per_thread=args.nodes_per_thread, pair_x=args.pair_x)
+                  nodes_per_thread=args.nodes_per_thread, pair_x=args.pair_x,
+                  trt_magic=3.0 / 16.0 if args.trt else 0.0)
     if kind == "dense":
         lat = lbm.Lattice(dims, (1, 1, 1), omega=1.7, **common)
         lat.set_geometry(None)
@@ -49,6 +52,18 @@ def setup(args):
     if kind == "pack":
         pack = inputs.sphere_pack(dims, 0.6, radius=8.0, seed=3)
         lat = lbm.Lattice(dims, (1, 1, 1), omega=1.0, force=(1e-6, 0, 0), **common)
+        lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
+        lat.init()
+        return lat
+    if kind == "channel":
+        d, per = inputs.paper_channel()
+        lat = lbm.Lattice(d, per, omega=1.0, force=(1e-6, 0, 0), **common)
+        lat.set_geometry(None)
+        lat.init()
+        return lat
+    if kind == "bed":
+        pack = inputs.paper_packed_bed()
+        lat = lbm.Lattice(pack.dims, pack.periodic, omega=1.0, force=(1e-6, 0, 0), **common)
         lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
         lat.init()
         return lat
@@ -73,6 +88,7 @@ def main(argv=None):
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--nodes-per-thread", type=int, default=0)
     ap.add_argument("--pair-x", type=int, default=0, help="AA on a full grid: 1 = two x-adjacent nodes per thread")
+    ap.add_argument("--trt", action="store_true", help="two-relaxation-time collision, magic 3/16")
     args = ap.parse_args(argv)
     import torch
 
