@@ -55,10 +55,15 @@ def measured_peaks():
     return FALLBACK_HBM, "fallback"
 
 
-def kernel_source_hash():
+HEADLINE_SOURCES = ("lbm_core.cuh", "lbm_dispatch.cuh", "lbm_steps.cuh", "lbm_steps_f32.cu")
+
+
+def kernel_source_hash(names=HEADLINE_SOURCES):
+    """Hash of the files that define the headline kernels (k_aa_even/odd,
+    FP32): a profile's DRAM counters stay valid while this does not change."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1111_0922_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())

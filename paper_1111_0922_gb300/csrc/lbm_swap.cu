@@ -124,13 +124,15 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
       const bool in_x = dx == 0 || (dx < 0 ? lx > 0 : lx < ex - 1);
       const bool in_y = dy == 0 || (dy < 0 ? ly > 0 : ly < ey - 1);
       const bool in_z = dz == 0 || (dz < 0 ? lz > 0 : lz < ez - 1);
-      if (in_x && in_y && in_z) {
-        v[i] = S[i * TN + t + dx + sp.tx * (dy + sp.ty * dz)];  // inside the tile
-        continue;
-      }
-      const int src = nd.nb(p, OPP(i));
+      // source slot, or -1 across a wall or from a solid cell (the fast path
+      // has neither: walls lie on tile faces and there is no solid cell)
+      const int src = nd.fast ? nd.nb_fast(p, OPP(i)) : nd.nb(p, OPP(i));
       if (src < 0) {
         v[i] = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
+        continue;
+      }
+      if (in_x && in_y && in_z) {
+        v[i] = S[i * TN + t + dx + sp.tx * (dy + sp.ty * dz)];  // inside the tile
         continue;
       }
       const int bit = tile_bit(in_x ? 0 : dx, in_y ? 0 : dy, in_z ? 0 : dz);
