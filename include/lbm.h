@@ -102,6 +102,10 @@ typedef struct lbm_config {
   int32_t pair_x;            /* LBM_AA, full grid, SoA: 1 = two x-adjacent nodes per thread with vector
                                 accesses where possible (periodic x, even nx, no solid cell);
                                 0 = one node per thread (default, faster on GB300) */
+  int32_t store_hint;        /* LBM_OS_PUSH / LBM_OS_PULL, SoA: 1 = write the second lattice with
+                                cache-streaming (evict-first) stores, the GPU counterpart of the
+                                non-temporal stores of OS-NT (Sec. 3); 0 = ordinary stores */
+  int32_t reserved;          /* must be 0 */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

@@ -338,6 +338,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->cg_shift < 0 || (cfg->addressing == LBM_DIRECT && cfg->cg_shift == 1))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift: >= 2 planes on a full grid, >= 1 node on a node list");
   if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
+  if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
+  if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint = 1 needs LBM_OS_PUSH or LBM_OS_PULL with LBM_SOA");
+  if (cfg->reserved != 0) return fail(nullptr, LBM_ERR_INVALID_ARG, "reserved must be 0");
 
   lbm_t *h = new lbm_t();
   h->cfg = *cfg;
@@ -965,7 +969,7 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
     case LBM_OS_PUSH:
     case LBM_OS_PULL: {
       StepParams p = params_of(h);
-      launch_step_kernel(v == LBM_OS_PUSH ? VAR_OS_PUSH : VAR_OS_PULL, 0, p, k, L);
+      launch_step_kernel(v == LBM_OS_PUSH ? VAR_OS_PUSH : VAR_OS_PULL, h->cfg.store_hint ? 2 : 0, p, k, L);
       std::swap(h->d_A, h->d_B);
       break;
     }

@@ -64,7 +64,9 @@ struct CodecF16S {
 // ---------------------------------------------------------------------------
 // PDF layouts.  SoA: array k holds slot s at k * npad + s (each array starts
 // on a 256-byte boundary).  AoS: the 19 PDFs of slot s are contiguous.
-template <class C, int AOS>
+// CS: stores use the cache-streaming policy (st.global.cs, evict-first), the
+// GPU counterpart of the non-temporal stores of the paper's OS-NT (Sec. 3).
+template <class C, int AOS, bool CS = false>
 struct Lattice {
   typename C::S *p;
   int64_t npad;
@@ -73,7 +75,12 @@ struct Lattice {
     return AOS ? p + s * Q + k : p + (int64_t)k * npad + s;
   }
   __device__ __forceinline__ typename C::T ld(int k, int64_t s) const { return C::dec(*at(k, s), inv_scale); }
-  __device__ __forceinline__ void st(int k, int64_t s, typename C::T v) const { *at(k, s) = C::enc(v, scale); }
+  __device__ __forceinline__ void st(int k, int64_t s, typename C::T v) const {
+    if constexpr (CS)
+      __stcs(at(k, s), C::enc(v, scale));
+    else
+      *at(k, s) = C::enc(v, scale);
+  }
 };
 
 // ---------------------------------------------------------------------------

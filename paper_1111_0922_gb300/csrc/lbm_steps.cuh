@@ -13,9 +13,9 @@
 
 namespace lbmk {
 
-template <class C, int AOS>
-__device__ __forceinline__ Lattice<C, AOS> lattice_of(void *p, const StepParams &P) {
-  Lattice<C, AOS> L;
+template <class C, int AOS, bool CS = false>
+__device__ __forceinline__ Lattice<C, AOS, CS> lattice_of(void *p, const StepParams &P) {
+  Lattice<C, AOS, CS> L;
   L.p = static_cast<typename C::S *>(p);
   L.npad = P.npad;
   L.scale = P.scale;
@@ -112,9 +112,9 @@ __global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
 
 // One-step push (Fig. 1a,b): read A at the node, write B at the neighbours.
 // FAST: the node has no solid or wall link (no bounce-back branch).
-template <bool FAST, class C, int AOS, class Node, bool FORCE>
+template <bool FAST, class C, int AOS, class Node, bool FORCE, class LB>
 __device__ __forceinline__ void os_push_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
-                                             const Lattice<C, AOS> &B, double &m, double &j) {
+                                             const LB &B, double &m, double &j) {
   using T = typename C::T;
   T d[Q];
 #pragma unroll
@@ -132,10 +132,10 @@ __device__ __forceinline__ void os_push_node(const StepParams &p, Node &nd, cons
   }
 }
 
-template <class C, int AOS, class Node, bool FORCE, bool RED>
+template <class C, int AOS, class Node, bool FORCE, bool RED, bool CS>
 __global__ void LBM_STEP_BOUNDS k_os_push(StepParams p) {
   const auto A = lattice_of<C, AOS>(p.A, p);
-  const auto B = lattice_of<C, AOS>(p.B, p);
+  const auto B = lattice_of<C, AOS, CS>(p.B, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
@@ -150,9 +150,9 @@ __global__ void LBM_STEP_BOUNDS k_os_push(StepParams p) {
 
 // One-step pull (Fig. 1c,d): gather from the neighbours in A, write B at the
 // node.  The stored state is post-collision.
-template <bool FAST, class C, int AOS, class Node, bool FORCE>
+template <bool FAST, class C, int AOS, class Node, bool FORCE, class LB>
 __device__ __forceinline__ void os_pull_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
-                                             const Lattice<C, AOS> &B, double &m, double &j) {
+                                             const LB &B, double &m, double &j) {
   using T = typename C::T;
   T d[Q];
   d[0] = A.ld(0, nd.s);
@@ -167,10 +167,10 @@ __device__ __forceinline__ void os_pull_node(const StepParams &p, Node &nd, cons
   for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
 }
 
-template <class C, int AOS, class Node, bool FORCE, bool RED>
+template <class C, int AOS, class Node, bool FORCE, bool RED, bool CS>
 __global__ void LBM_STEP_BOUNDS k_os_pull(StepParams p) {
   const auto A = lattice_of<C, AOS>(p.A, p);
-  const auto B = lattice_of<C, AOS>(p.B, p);
+  const auto B = lattice_of<C, AOS, CS>(p.B, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
@@ -342,13 +342,24 @@ struct LaunchTS {
       k_ts_stream<C, AOS, NodeOf<IND>><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
+// sub: bit 0 = push (else pull), bit 1 = streaming stores (SoA only)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchOS {
-  static void run(const StepParams &p, int push, const LaunchShape &L) {
+  template <bool CS>
+  static void go(const StepParams &p, bool push, const LaunchShape &L) {
     if (push)
-      k_os_push<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      k_os_push<C, AOS, NodeOf<IND>, FORCE, RED, CS><<<L.grid, L.block, 0, L.stream>>>(p);
     else
-      k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED, CS><<<L.grid, L.block, 0, L.stream>>>(p);
+  }
+  static void run(const StepParams &p, int sub, const LaunchShape &L) {
+    if constexpr (AOS == 0) {
+      if (sub & 2) {
+        go<true>(p, sub & 1, L);
+        return;
+      }
+    }
+    go<false>(p, sub & 1, L);
   }
 };
 // sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full grid)
@@ -384,10 +395,10 @@ void launch_step_kernel_t(int variant, int sub, const StepParams &p, const Kerne
       dispatch_layout<LaunchTS, C>(k.aos, k.ind, k.force, k.red, p, sub, L);
       break;
     case VAR_OS_PUSH:
-      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, 1, L);
+      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, 1 | (sub & 2), L);
       break;
     case VAR_OS_PULL:
-      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, 0, L);
+      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, sub & 2, L);
       break;
     case VAR_AA:
       dispatch_layout<LaunchAA, C>(k.aos, k.ind, k.force, k.red, p, sub, L);

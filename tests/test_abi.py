@@ -42,8 +42,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes(lib):
     from paper_1111_0922_gb300 import lbm
 
-    # 3+3+4 int32, 6 doubles, 4 int32, 4 pointers
-    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 4 * 4 + 4 * 8
+    # 3+3+4 int32, 6 doubles, 6 int32, 4 pointers
+    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 6 * 4 + 4 * 8
     assert ctypes.sizeof(lbm.lbm_info) == 6 * 8 + 2 * 4 + 8 + 2 * 4
 
 
@@ -62,6 +62,16 @@ def test_host_only_calls(lib):
     bad = lbm.lbm_config_default()
     bad.periodic[1] = 1
     bad.ny = 1
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_create(bad)
+    for variant, layout in ((lbm.LBM_AA, lbm.LBM_SOA), (lbm.LBM_OS_PULL, lbm.LBM_AOS)):
+        bad = lbm.lbm_config_default()
+        bad.variant, bad.layout, bad.store_hint = variant, layout, 1
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_create(bad)
+        assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    bad = lbm.lbm_config_default()
+    bad.reserved = 1
     with pytest.raises(lbm.LBMError):
         lbm.lbm_create(bad)
     assert lib.lbm_destroy(None) == 0

@@ -349,3 +349,31 @@ def test_compressed_grid_node_list_slabs(lbm, slab, per):
     out = lat.pdfs()
     assert np.max(np.abs(out - ref[:, cells]) / ref[:, cells]) <= 1e-12
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("addressing", ["direct", "indirect"])
+@pytest.mark.parametrize("variant", ["os_push", "os_pull"])
+def test_streaming_stores_match(lbm, variant, addressing, precision):
+    """OS push/pull with cache-streaming stores of the second lattice (the
+    OS-NT analogue): the same arithmetic as ordinary stores, so the PDFs agree
+    bit for bit, and with the oracle within the precision's tolerance."""
+    dims, per = (19, 13, 11), (1, 0, 1)
+    solid, f0 = _case(dims, 0.12, seed=37)
+    g = (2e-5, -1e-5, 5e-6)
+    ref = oracle.run_push(dims, per, solid, f0, 5, 1.3, g)
+    fl = solid == 0
+    outs = []
+    for hint in (0, 1):
+        lat = _lattice(lbm, dims, per, variant, addressing, "soa", precision, 1.3, g, store_hint=hint)
+        lat.set_geometry(solid)
+        cells = lat.nodes() if addressing == "indirect" else None
+        lat.set_pdfs(f0 if cells is None else f0[:, cells])
+        lat.step(5)
+        outs.append(lat.pdfs())
+        lat.close()
+    assert np.array_equal(outs[0], outs[1])
+    if addressing == "direct":
+        _compare(precision, outs[1], ref, g, fl)
+    else:
+        _compare(precision, outs[1], ref[:, np.flatnonzero(fl)], g, slice(None))
