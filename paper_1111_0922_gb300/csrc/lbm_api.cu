@@ -31,6 +31,7 @@ struct lbm {
   int64_t ipad = 0;
   uint8_t *d_solid = nullptr;
   bool any_solid = false;
+  bool idx_folded = false;  // AA pattern, SoA node list: solid links folded into IDX
   int32_t *d_cells = nullptr, *d_idx = nullptr, *d_etidx = nullptr;
   void *d_A = nullptr, *d_B = nullptr;
   size_t state_bytes = 0;
@@ -193,10 +194,13 @@ static StepParams params_of(const lbm_t *h) {
   p.gx = h->cfg.force[0];
   p.gy = h->cfg.force[1];
   p.gz = h->cfg.force[2];
+  p.kf = make_collk<float>((float)p.omega, (float)p.omega_m, (float)p.gx, (float)p.gy, (float)p.gz);
+  p.kd = make_collk<double>(p.omega, p.omega_m, p.gx, p.gy, p.gz);
   p.scale = h->scale;
   p.inv_scale = 1.0f / h->scale;
   p.partials = h->d_partials;
   p.err = h->d_err;
+  p.idx_folded = h->idx_folded ? 1 : 0;
   return p;
 }
 
@@ -523,6 +527,12 @@ static lbm_status build_geometry(lbm_t *h) {
     return fail(h, LBM_ERR_OOM, "PDF storage of %zu bytes", h->state_bytes);
   CUDA_TRY(h, cudaMemsetAsync(h->d_A, 0, h->state_bytes, h->stream));
   if (h->d_B) CUDA_TRY(h, cudaMemsetAsync(h->d_B, 0, h->state_bytes, h->stream));
+  if (c.variant == LBM_AA && c.addressing == LBM_INDIRECT && c.layout == LBM_SOA && h->nodes > 0) {
+    launch_fold_idx(h->d_idx, h->ipad, h->nodes, h->npad, h->stream);
+    lbm_status st = check_launch(h, "fold_idx");
+    if (st != LBM_OK) return st;
+    h->idx_folded = true;
+  }
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
   int64_t need = std::max<int64_t>(blocks_of(L), reduce_blocks_for(h->nn));
@@ -552,6 +562,7 @@ static void reset_geometry(lbm_t *h) {
   h->has_geometry = false;
   h->cells = (int64_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
   h->nodes = h->nghost = h->nn = h->slots = h->npad = h->ipad = 0;
+  h->idx_folded = false;
   h->steps = 0;
   for (int i = 0; i < Q; ++i) h->map[i] = i;
 }
@@ -654,6 +665,11 @@ lbm_status lbm_get_idx(lbm_t *h, int32_t *idx) {
   if (h->nodes > 0)
     CUDA_TRY(h, cudaMemcpy2D(idx, sizeof(int32_t) * h->nodes, h->d_idx, sizeof(int32_t) * h->ipad,
                              sizeof(int32_t) * h->nodes, 18, cudaMemcpyDeviceToHost));
+  if (h->idx_folded) {
+    // folded bounce-back slots lie outside [0, nodes): report them as -1
+    for (int64_t e = 0; e < 18 * h->nodes; ++e)
+      if (idx[e] < 0 || idx[e] >= h->nodes) idx[e] = -1;
+  }
   return LBM_OK;
 }
 

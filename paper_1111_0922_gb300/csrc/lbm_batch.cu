@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
   const BatchSlot &sl = p.slots[w.x];
   const int64_t end = sl.start + sl.nodes;
   const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const T omega = T(sl.omega), omega_m = T(sl.omega_m), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
+  const CollK<T> K = make_collk<T>(T(sl.omega), T(sl.omega_m), T(sl.gx), T(sl.gy), T(sl.gz));
   double m = 0.0, j = 0.0;
 #pragma unroll
   for (int r = 0; r < NPT; ++r) {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
     if (!odd) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) d[i] = A.ld(i, s);
-      collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
+      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
       const int s2 = launder(s);
 #pragma unroll
       for (int i = 0; i < Q; ++i) A.st(OPP(i), s2, d[i]);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
         const int src = __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.npad + s);
         d[i] = src >= 0 ? A.ld(OPP(i), src) : A.ld(i, s);
       }
-      collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
+      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
       const int s2 = launder(s);
       A.st(0, s2, d[0]);
 #pragma unroll
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_et(BatchParams p) 
   const BatchSlot &sl = p.slots[w.x];
   const int64_t end = sl.start + sl.nodes;
   const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const T omega = T(sl.omega), omega_m = T(sl.omega_m), gx = T(sl.gx), gy = T(sl.gy), gz = T(sl.gz);
+  const CollK<T> K = make_collk<T>(T(sl.omega), T(sl.omega_m), T(sl.gx), T(sl.gy), T(sl.gz));
   double m = 0.0, j = 0.0;
 #pragma unroll
   for (int r = 0; r < NPT; ++r) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_et(BatchParams p) 
       d[i + 1] = A.ld(ai1, (int)(wd[k] & 0x7fffffffu));
     }
     T drho, rjx;
-    collide<T, true>(d, omega, omega_m, gx, gy, gz, drho, rjx);
+    collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
     const int s2 = launder(s);
 #pragma unroll
     for (int k = 1; k <= 9; ++k) wd[k] = (uint32_t)launder((int)wd[k]);
@@ -244,7 +244,7 @@ __global__ void k_batch_get(BatchParams p, int slot, int variant, double *f_nat)
         arr = odd ? OPP(i) : i;
         if (!(i & 1)) pos = (int)((uint32_t)__ldg(p.idx + (int64_t)((i - 2) / 2) * p.npad + s) & 0x7fffffffu);
       }
-      f_nat[(int64_t)i * sl.nodes + k] = WD(i) + (double)A.ld(arr, pos);
+      f_nat[(int64_t)i * sl.nodes + k] = WD(i) + (double)A.ld_dev(arr, pos);
     }
   }
 }

@@ -41,7 +41,7 @@ __device__ __forceinline__ void cg_node(const StepParams &p, DirectNode &nd, con
     d[i] = (FAST || src >= 0) ? A.ld(i, src) : A.ld(OPP(i), nd.s);
   }
   T drho, rjx;
-  collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+  collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
   m += 1.0 + (double)drho;
   j += (double)rjx;
   nd.launder_all();
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256, (step_min_cg<C>())) k_cg_ind_slab(StepPar
       d[i] = src != kCgSolid ? A.ld(i, src) : A.ld(OPP(i), n);
     }
     T drho, rjx;
-    collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+    collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
     m += 1.0 + (double)drho;
     j += (double)rjx;
     const int w = launder(n);

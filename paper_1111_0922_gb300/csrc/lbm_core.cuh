@@ -37,12 +37,19 @@ __host__ __device__ constexpr double WD(int i) {
 // Storage codecs.  Every precision stores the deviation d_i = f_i - w_i
 // (rho0 = 1).  F16S stores round(d_i * S) with a power-of-two S, so decoding
 // is exact and only the final rounding to FP16 loses precision.
+//   raw / unraw: stored value <-> compute type without the scale; the step
+//                kernels work on S * d_i throughout (the collision takes S,
+//                so no per-PDF multiply is spent on the scale).
+//   dec / enc:   stored value <-> d_i (state upload, read-out, reductions).
 // kMinBlocks: resident 256-thread blocks per SM the step kernels are built
 // for (a register budget: 2 -> 128, 3 -> 85 registers per thread).
 struct CodecF64 {
   using S = double;  // stored
   using T = double;  // computed
   static constexpr int kMinBlocks = 2;
+  static constexpr bool kScaled = false;
+  __device__ static __forceinline__ T raw(S v) { return v; }
+  __device__ static __forceinline__ S unraw(T v) { return v; }
   __device__ static __forceinline__ T dec(S v, float) { return v; }
   __device__ static __forceinline__ S enc(T v, float) { return v; }
 };
@@ -50,6 +57,9 @@ struct CodecF32 {
   using S = float;
   using T = float;
   static constexpr int kMinBlocks = 3;
+  static constexpr bool kScaled = false;
+  __device__ static __forceinline__ T raw(S v) { return v; }
+  __device__ static __forceinline__ S unraw(T v) { return v; }
   __device__ static __forceinline__ T dec(S v, float) { return v; }
   __device__ static __forceinline__ S enc(T v, float) { return v; }
 };
@@ -57,6 +67,9 @@ struct CodecF16S {
   using S = __half;
   using T = float;
   static constexpr int kMinBlocks = 3;
+  static constexpr bool kScaled = true;
+  __device__ static __forceinline__ T raw(S v) { return __half2float(v); }
+  __device__ static __forceinline__ S unraw(T v) { return __float2half_rn(v); }
   __device__ static __forceinline__ T dec(S v, float inv_scale) { return __half2float(v) * inv_scale; }
   __device__ static __forceinline__ S enc(T v, float scale) { return __float2half_rn(v * scale); }
 };
@@ -74,13 +87,17 @@ struct Lattice {
   __device__ __forceinline__ typename C::S *at(int k, int64_t s) const {
     return AOS ? p + s * Q + k : p + (int64_t)k * npad + s;
   }
-  __device__ __forceinline__ typename C::T ld(int k, int64_t s) const { return C::dec(*at(k, s), inv_scale); }
+  // step kernels: values in the collision's units (S * d_i for F16S)
+  __device__ __forceinline__ typename C::T ld(int k, int64_t s) const { return C::raw(*at(k, s)); }
   __device__ __forceinline__ void st(int k, int64_t s, typename C::T v) const {
     if constexpr (CS)
-      __stcs(at(k, s), C::enc(v, scale));
+      __stcs(at(k, s), C::unraw(v));
     else
-      *at(k, s) = C::enc(v, scale);
+      *at(k, s) = C::unraw(v);
   }
+  // state upload and read-out: the deviation d_i itself
+  __device__ __forceinline__ typename C::T ld_dev(int k, int64_t s) const { return C::dec(*at(k, s), inv_scale); }
+  __device__ __forceinline__ void st_dev(int k, int64_t s, typename C::T v) const { *at(k, s) = C::enc(v, scale); }
 };
 
 // ---------------------------------------------------------------------------
@@ -151,16 +168,82 @@ __device__ __forceinline__ int64_t grid_position(const Grid &g, int x, int y, in
 //     a* = a - lp (a - a_eq) + F+,  b* = b - lm (b - b_eq) + F-
 //     d*_i = a* + b*,  d*_opp = a* - b*
 //   rest: d*_0 = d_0 - lp (d_0 - w_0 [(rho - 1) - 1.5 rho u.u]) - (1 - lp/2) w_0 rho 3 u.g
-// Returns rho - 1 and rho u_x (for the mass and flux reductions).
+//
+// Evaluated with the terms regrouped so that each pair costs about ten
+// operations: with A = lp (rho - 1) - rho (1.5 lp u.u + 3 (1 - lp/2) u.g),
+//   a* = (1 - lp)/2 (d_i + d_opp) + w_i A + rho (c.u) (4.5 lp w_i c.u + 9 (1 - lp/2) w_i c.g)
+//   b* = (1 - lm)/2 (d_i - d_opp) + rho (3 lm w_i c.u + 3 (1 - lm/2) w_i c.g)
+//   d*_0 = (1 - lp) d_0 + w_0 A
+// and for BGK d*_i = (1 - lp) d_i + (w_i A + ...) +- (...), which keeps
+// lp = 0 (no collision) an exact identity.
+//
+// The d_i arrive multiplied by the storage scale s (a power of two: 1, or S
+// for F16S) and leave multiplied by it; the moments are unscaled exactly with
+// inv_s.  Returns rho - 1 and rho u_x (for the mass and flux reductions).
+// Per-launch constants of the collision, uniform over the nodes: filled once
+// on the host for a lattice's launches (kernel parameters, read by the node
+// arithmetic as constant operands), or per thread for a batch segment.
+template <typename T>
+struct CollK {
+  T lp, om1;         // symmetric rate, 1 - lp
+  T al, be;          // TRT: (1 - lp)/2 + (1 - lm)/2, (1 - lp)/2 - (1 - lm)/2
+  T q15, q3;         // 1.5 lp, 3 (1 - lp/2)
+  T tp[2], tm[2];    // 4.5 lp w, 3 lm w for w = 1/18, 1/36
+  T fp[10], fm[10];  // pair k (odd member 2k-1): 9 (1 - lp/2) w c.g, 3 (1 - lm/2) w c.g
+  T hg[3], g[3];     // g/2, g
+  int bgk;           // lm == lp
+};
+
+template <typename T>
+__host__ __device__ inline CollK<T> make_collk(T lp, T lm, T gx, T gy, T gz) {
+  CollK<T> K;
+  const T kp = T(1) - T(0.5) * lp, km = T(1) - T(0.5) * lm;
+  K.lp = lp;
+  K.om1 = T(1) - lp;
+  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);
+  K.al = hp + hm;
+  K.be = hp - hm;
+  K.q15 = T(1.5) * lp;
+  K.q3 = T(3) * kp;
+  const T w[2] = {T(1) / T(18), T(1) / T(36)};
+  for (int c = 0; c < 2; ++c) {
+    K.tp[c] = T(4.5) * lp * w[c];
+    K.tm[c] = T(3) * lm * w[c];
+  }
+  K.fp[0] = K.fm[0] = T(0);
+  for (int k = 1; k <= 9; ++k) {
+    const int i = 2 * k - 1;
+    const T cg = T(CX(i)) * gx + T(CY(i)) * gy + T(CZ(i)) * gz;
+    const T wi = i <= 6 ? w[0] : w[1];
+    K.fp[k] = T(9) * kp * wi * cg;
+    K.fm[k] = T(3) * km * wi * cg;
+  }
+  K.g[0] = gx;
+  K.g[1] = gy;
+  K.g[2] = gz;
+  for (int a = 0; a < 3; ++a) K.hg[a] = T(0.5) * K.g[a];
+  K.bgk = lm == lp;
+  return K;
+}
+
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  return T(1) / x;
+}
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  return __fdividef(1.0f, x);  // rho is near 1: the fast reciprocal is well within FP32 parity
+}
+
 template <typename T, bool FORCE>
-__device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz, T &drho_out, T &rjx_out) {
+__device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
   T sum[10], dif[10];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     sum[k] = d[2 * k - 1] + d[2 * k];
     dif[k] = d[2 * k - 1] - d[2 * k];
   }
-  const T drho = d[0] + (((sum[1] + sum[2]) + (sum[3] + sum[4])) + ((sum[5] + sum[6]) + (sum[7] + sum[8])) + sum[9]);
+  const T sdrho = d[0] + (((sum[1] + sum[2]) + (sum[3] + sum[4])) + ((sum[5] + sum[6]) + (sum[7] + sum[8])) + sum[9]);
   // pair k = (2k-1, 2k); velocity of the odd member
   T jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -173,14 +256,17 @@ __device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz,
     if (CZ(i) == 1) jz += dif[k];
     if (CZ(i) == -1) jz -= dif[k];
   }
+  const T drho = sdrho * inv_s;
+  jx *= inv_s;
+  jy *= inv_s;
+  jz *= inv_s;
   const T rho = T(1) + drho;
-  const T inv = T(1) / rho;
+  const T inv = recip(rho);
   T ux, uy, uz;
   if (FORCE) {
-    const T hr = T(0.5) * rho;
-    ux = (jx + hr * gx) * inv;
-    uy = (jy + hr * gy) * inv;
-    uz = (jz + hr * gz) * inv;
+    ux = (jx + rho * K.hg[0]) * inv;
+    uy = (jy + rho * K.hg[1]) * inv;
+    uz = (jz + rho * K.hg[2]) * inv;
   } else {
     ux = jx * inv;
     uy = jy * inv;
@@ -188,63 +274,64 @@ __device__ __forceinline__ void collide(T (&d)[Q], T lp, T lm, T gx, T gy, T gz,
   }
   drho_out = drho;
   rjx_out = rho * ux;
-  const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-  const T kp = T(1) - T(0.5) * lp;
-  T ug = 0;
-  if (FORCE) ug = ux * gx + uy * gy + uz * gz;
-  {
-    const T w = T(WD(0));
-    T v = (T(1) - lp) * d[0] + lp * w * (drho - rho * usq15);
-    if (FORCE) v -= kp * w * rho * T(3) * ug;
-    d[0] = v;
-  }
-  if (lm == lp) {
-    // BGK: d*_i = (1 - omega) d_i + omega d_eq,i (+ F_i), per pair
-    const T om1 = T(1) - lp;
+  T q = K.q15 * (ux * ux + uy * uy + uz * uz);
+  if (FORCE) q += K.q3 * (ux * K.g[0] + uy * K.g[1] + uz * K.g[2]);
+  const T srho = s * rho;
+  const T sA = K.lp * sdrho - srho * q;  // s * A
+  d[0] = K.om1 * d[0] + T(WD(0)) * sA;
+  const T wsA[2] = {T(WD(1)) * sA, T(WD(7)) * sA};
+  // P = s (w_i A + rho (c.u)(...)), M = s rho (...) of pair k
+  auto terms = [&](int k, T &P, T &M) {
+    const int i = 2 * k - 1;
+    const int c = i <= 6 ? 0 : 1;
+    T cu = 0;
+    if (CX(i)) cu += T(CX(i)) * ux;
+    if (CY(i)) cu += T(CY(i)) * uy;
+    if (CZ(i)) cu += T(CZ(i)) * uz;
+    T tp = K.tp[c] * cu;
+    T tm = K.tm[c] * cu;
+    if (FORCE) {
+      tp += K.fp[k];
+      tm += K.fm[k];
+    }
+    P = wsA[c] + srho * (cu * tp);
+    M = srho * tm;
+  };
+  if (K.bgk) {
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
       const int i = 2 * k - 1;
-      const T w = T(WD(i));
-      T cu = 0, cg = 0;
-      if (CX(i)) { cu += T(CX(i)) * ux; if (FORCE) cg += T(CX(i)) * gx; }
-      if (CY(i)) { cu += T(CY(i)) * uy; if (FORCE) cg += T(CY(i)) * gy; }
-      if (CZ(i)) { cu += T(CZ(i)) * uz; if (FORCE) cg += T(CZ(i)) * gz; }
-      const T sym = drho + rho * (T(4.5) * cu * cu - usq15);
-      const T asym = T(3) * rho * cu;
-      T vp = om1 * d[i] + lp * w * (sym + asym);
-      T vm = om1 * d[i + 1] + lp * w * (sym - asym);
-      if (FORCE) {
-        const T fs = kp * w * rho * (T(9) * cu * cg - T(3) * ug);
-        const T fa = kp * w * rho * T(3) * cg;
-        vp += fs + fa;
-        vm += fs - fa;
-      }
-      d[i] = vp;
-      d[i + 1] = vm;
+      T P, M;
+      terms(k, P, M);
+      d[i] = K.om1 * d[i] + (P + M);
+      d[i + 1] = K.om1 * d[i + 1] + (P - M);
     }
-    return;
-  }
-  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);  // (1 - l)/2: a = sum/2, b = dif/2
-  const T km = T(1) - T(0.5) * lm;
+  } else {
+    // a* +- b* with a = (d_i + d_opp)/2, b = (d_i - d_opp)/2 expanded, so
+    // that only d_i and d_opp stay live:
+    //   d*_i = al d_i + be d_opp + (P + M),  d*_opp = be d_i + al d_opp + (P - M)
 #pragma unroll
-  for (int k = 1; k <= 9; ++k) {
-    const int i = 2 * k - 1;
-    const T w = T(WD(i));
-    T cu = 0, cg = 0;
-    if (CX(i)) { cu += T(CX(i)) * ux; if (FORCE) cg += T(CX(i)) * gx; }
-    if (CY(i)) { cu += T(CY(i)) * uy; if (FORCE) cg += T(CY(i)) * gy; }
-    if (CZ(i)) { cu += T(CZ(i)) * uz; if (FORCE) cg += T(CZ(i)) * gz; }
-    const T aeq = drho + rho * (T(4.5) * cu * cu - usq15);
-    const T beq = T(3) * rho * cu;
-    T a = hp * sum[k] + lp * w * aeq;
-    T b = hm * dif[k] + lm * w * beq;
-    if (FORCE) {
-      a += kp * w * rho * (T(9) * cu * cg - T(3) * ug);
-      b += km * w * rho * T(3) * cg;
+    for (int k = 1; k <= 9; ++k) {
+      const int i = 2 * k - 1;
+      T P, M;
+      terms(k, P, M);
+      const T di = d[i], dj = d[i + 1];
+      d[i] = K.al * di + (K.be * dj + (P + M));
+      d[i + 1] = K.al * dj + (K.be * di + (P - M));
     }
-    d[i] = a + b;
-    d[i + 1] = a - b;
   }
+}
+
+// The collision in the units a codec's step kernels load: S * d_i for F16S,
+// d_i otherwise (the scale is the literal 1 and folds away).
+template <class C, bool FORCE>
+__device__ __forceinline__ void collide_stored(typename C::T (&d)[Q], const CollK<typename C::T> &K, float scale,
+                                               float inv_scale, typename C::T &drho, typename C::T &rjx) {
+  using T = typename C::T;
+  if constexpr (C::kScaled)
+    collide<T, FORCE>(d, K, T(scale), T(inv_scale), drho, rjx);
+  else
+    collide<T, FORCE>(d, K, T(1), T(1), drho, rjx);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,13 +349,27 @@ struct StepParams {
   int map[Q];         // esoteric twist: physical array of direction i
   double omega, gx, gy, gz;
   double omega_m;     // antisymmetric rate (TRT); equal to omega for BGK
+  CollK<float> kf;    // collision constants for FP32 arithmetic (F32, F16S)
+  CollK<double> kd;   // ... for FP64
   float scale, inv_scale;
   double *partials;   // fused reduction: 2 doubles per block, or nullptr
   int *err;           // device error word
   int z0, z1;         // compressed grid: planes of this launch
   int zo_read, zo_write;  // compressed grid: plane offsets of the old and new state
   int64_t slab0, slab1;   // compressed grid on a node list: node numbers of this launch
+  int idx_folded;         // AA pattern, SoA node list: IDX holds bounce-back slots, no -1
 };
+
+template <typename T>
+__device__ __forceinline__ const CollK<T> &coll_of(const StepParams &p);
+template <>
+__device__ __forceinline__ const CollK<float> &coll_of<float>(const StepParams &p) {
+  return p.kf;
+}
+template <>
+__device__ __forceinline__ const CollK<double> &coll_of<double>(const StepParams &p) {
+  return p.kd;
+}
 
 // Hide a value's provenance from the optimiser: addresses derived from the
 // result are recomputed instead of kept live from an earlier phase (loads and
@@ -397,6 +498,7 @@ struct IndirectNode {
   __device__ __forceinline__ bool init_it(const StepParams &p, int64_t it) { return init(p, it); }
   __device__ __forceinline__ void launder_all() { s = launder(s); }
   static constexpr bool fast = false;
+  // FAST: the entry is used as a slot whatever it holds (folded IDX)
   template <bool FAST>
   __device__ __forceinline__ int nbf(const StepParams &p, int i) const { return nb(p, i); }
   __device__ __forceinline__ int nb(const StepParams &p, int i) const {

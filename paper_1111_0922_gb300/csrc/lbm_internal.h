@@ -84,6 +84,8 @@ int64_t build_node_list(const uint8_t *solid, int64_t ncell, int32_t *node_of, i
 int64_t scan_scratch_elems(int64_t n);
 void launch_build_idx(const int32_t *cells, const int32_t *node_of, int64_t N, int nx, int ny, int nz,
                       const int *periodic, int32_t *idx, int64_t ipad, cudaStream_t s);
+// AA pattern, SoA: solid links of IDX replaced by their bounce-back slots
+void launch_fold_idx(int32_t *idx, int64_t ipad, int64_t N, int64_t npad, cudaStream_t s);
 // esoteric twist packed index; ghost_map is (nx+2)(ny+2)(nz+2) int32 scratch
 int64_t build_et_index(const int32_t *cells, const int32_t *node_of, int64_t N, int nx, int ny, int nz,
                        const int *periodic, int32_t *ghost_map, int32_t *etidx, int64_t ipad,

@@ -32,17 +32,17 @@ struct PairIO {
   float scale, inv_scale;
   __device__ __forceinline__ void ld2(int k, int64_t s0, T &a, T &b) const {
     const V v = *reinterpret_cast<const V *>(p + (int64_t)k * npad + s0);
-    a = C::dec(v.x, inv_scale);
-    b = C::dec(v.y, inv_scale);
+    a = C::raw(v.x);
+    b = C::raw(v.y);
   }
   __device__ __forceinline__ void st2(int k, int64_t s0, T a, T b) const {
     V v;
-    v.x = C::enc(a, scale);
-    v.y = C::enc(b, scale);
+    v.x = C::unraw(a);
+    v.y = C::unraw(b);
     *reinterpret_cast<V *>(p + (int64_t)k * npad + s0) = v;
   }
-  __device__ __forceinline__ T ld1(int k, int64_t s) const { return C::dec(p[(int64_t)k * npad + s], inv_scale); }
-  __device__ __forceinline__ void st1(int k, int64_t s, T a) const { p[(int64_t)k * npad + s] = C::enc(a, scale); }
+  __device__ __forceinline__ T ld1(int k, int64_t s) const { return C::raw(p[(int64_t)k * npad + s]); }
+  __device__ __forceinline__ void st1(int k, int64_t s, T a) const { p[(int64_t)k * npad + s] = C::unraw(a); }
 };
 
 // Row geometry of one thread's pair.
@@ -73,8 +73,8 @@ __device__ __forceinline__ void pair_collide(typename C::T (&d0)[Q], typename C:
                                              double &m, double &j) {
   using T = typename C::T;
   T r0, j0, r1, j1;
-  collide<T, FORCE>(d0, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), r0, j0);
-  collide<T, FORCE>(d1, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), r1, j1);
+  collide_stored<C, FORCE>(d0, coll_of<T>(p), p.scale, p.inv_scale, r0, j0);
+  collide_stored<C, FORCE>(d1, coll_of<T>(p), p.scale, p.inv_scale, r1, j1);
   m += 2.0 + (double)r0 + (double)r1;
   j += (double)j0 + (double)j1;
 }

@@ -224,6 +224,28 @@ void launch_build_idx(const int32_t *cells, const int32_t *node_of, int64_t N, i
                                                idx, ipad);
 }
 
+// Bounce-back folded into IDX for the AA pattern on SoA storage: a solid
+// link k of node s becomes the slot that, in the array the odd step uses with
+// IDX[k], lands on the node's own slot of the reflected direction:
+//   read  f_opp(k)(x) <- array k at IDX[k], BB: array opp(k) at s
+//   write g_k(x)      -> array k at IDX[k], BB: array opp(k) at s
+// so IDX'[k][s] = s + (opp(k) - k) npad in both cases.  Values are < 0 or
+// >= npad (>= the node count) exactly for folded links.
+__global__ void k_fold_idx(int32_t *idx, int64_t ipad, int64_t N, int64_t npad) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 1; k < Q; ++k) {
+      int32_t &v = idx[(int64_t)(k - 1) * ipad + s];
+      if (v < 0) v = (int32_t)(s + (int64_t)(OPP(k) - k) * npad);
+    }
+  }
+}
+
+void launch_fold_idx(int32_t *idx, int64_t ipad, int64_t N, int64_t npad, cudaStream_t s) {
+  if (N == 0) return;
+  k_fold_idx<<<grid_for(N, 256), 256, 0, s>>>(idx, ipad, N, npad);
+}
+
 // ---------------------------------------------------------------------------
 // Esoteric twist index.  Position x + c_i (odd i) on an extended box with a
 // one-cell margin: wrapped on periodic axes, in the margin beyond a wall.

@@ -95,7 +95,7 @@ __global__ void k_put_state(StepParams p, const double *f_nat, const double *rho
     for (int i = 0; i < Q; ++i) {
       int arr, pos;
       ns.template where<M>(p, i, arr, pos);
-      L.st(arr, pos, (T)(f[i] - WD(i)));
+      L.st_dev(arr, pos, (T)(f[i] - WD(i)));
     }
   }
 }
@@ -107,7 +107,7 @@ __device__ __forceinline__ void read_natural(const StepParams &p, const NodeSlot
   for (int i = 0; i < Q; ++i) {
     int arr, pos;
     ns.template where<M>(p, i, arr, pos);
-    f[i] = WD(i) + (double)L.ld(arr, pos);
+    f[i] = WD(i) + (double)L.ld_dev(arr, pos);
   }
 }
 

@@ -43,10 +43,11 @@ constexpr int step_min_blocks() {
 template <bool IND>
 using NodeOf = typename std::conditional<IND, IndirectNode, DirectNode>::type;
 
-template <typename T, bool FORCE>
-__device__ __forceinline__ void run_collision(T (&d)[Q], const StepParams &p, double &m, double &j) {
+template <class C, bool FORCE>
+__device__ __forceinline__ void run_collision(typename C::T (&d)[Q], const StepParams &p, double &m, double &j) {
+  using T = typename C::T;
   T drho, rjx;
-  collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+  collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
   m += 1.0 + (double)drho;
   j += (double)rjx;
 }
@@ -69,7 +70,7 @@ __global__ void LBM_STEP_BOUNDS k_ts_collide(StepParams p) {
     T d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
-    run_collision<T, FORCE>(d, p, m, j);
+    run_collision<C, FORCE>(d, p, m, j);
     nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
@@ -119,7 +120,7 @@ __device__ __forceinline__ void os_push_node(const StepParams &p, Node &nd, cons
   T d[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
-  run_collision<T, FORCE>(d, p, m, j);
+  run_collision<C, FORCE>(d, p, m, j);
   nd.launder_all();
   B.st(0, nd.s, d[0]);
 #pragma unroll
@@ -161,7 +162,7 @@ __device__ __forceinline__ void os_pull_node(const StepParams &p, Node &nd, cons
     const int src = nd.template nbf<FAST>(p, OPP(i));
     d[i] = (FAST || src >= 0) ? A.ld(i, src) : A.ld(OPP(i), nd.s);
   }
-  run_collision<T, FORCE>(d, p, m, j);
+  run_collision<C, FORCE>(d, p, m, j);
   nd.launder_all();
 #pragma unroll
   for (int i = 0; i < Q; ++i) B.st(i, nd.s, d[i]);
@@ -196,7 +197,7 @@ __global__ void LBM_STEP_BOUNDS k_aa_even(StepParams p) {
     T d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = A.ld(i, nd.s);
-    run_collision<T, FORCE>(d, p, m, j);
+    run_collision<C, FORCE>(d, p, m, j);
     nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) A.st(OPP(i), nd.s, d[i]);
@@ -232,7 +233,7 @@ __device__ __forceinline__ void aa_odd_node(const StepParams &p, Node &nd, const
     const int src = kHold ? nb[OPP(i)] : nd.template nbf<FAST>(p, OPP(i));
     d[i] = (FAST || src >= 0) ? A.ld(OPP(i), src) : A.ld(i, nd.s);
   }
-  run_collision<T, FORCE>(d, p, m, j);
+  run_collision<C, FORCE>(d, p, m, j);
   nd.launder_all();
   A.st(0, nd.s, d[0]);
 #pragma unroll
@@ -245,6 +246,11 @@ __device__ __forceinline__ void aa_odd_node(const StepParams &p, Node &nd, const
   }
 }
 
+// Nodes the odd step may treat as having no bounce-back branch: full-grid
+// nodes without wall or solid links, every node of a folded IDX.
+__device__ __forceinline__ bool aa_fast(const DirectNode &nd, const StepParams &) { return nd.fast; }
+__device__ __forceinline__ bool aa_fast(const IndirectNode &, const StepParams &p) { return p.idx_folded != 0; }
+
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   const auto A = lattice_of<C, AOS>(p.A, p);
@@ -252,7 +258,7 @@ __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    if (nd.fast)
+    if (aa_fast(nd, p))
       aa_odd_node<true, C, AOS, Node, FORCE>(p, nd, A, m, j);
     else
       aa_odd_node<false, C, AOS, Node, FORCE>(p, nd, A, m, j);
@@ -301,7 +307,7 @@ __global__ void LBM_STEP_BOUNDS_IND k_et(StepParams p) {
       const int pos = IND ? (int)(w[k] & 0x7fffffffu) : et_pos(nd, p, i);
       d[i + 1] = A.ld(p.map[i + 1], pos);
     }
-    run_collision<T, FORCE>(d, p, m, j);
+    run_collision<C, FORCE>(d, p, m, j);
     nd.launder_all();
     if (IND) {
 #pragma unroll

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
     T drho, rjx;
-    collide<T, FORCE>(d, T(p.omega), T(p.omega_m), T(p.gx), T(p.gy), T(p.gz), drho, rjx);
+    collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
     m = 1.0 + (double)drho;
     jsum = (double)rjx;
 #pragma unroll
