@@ -177,9 +177,45 @@ __device__ __forceinline__ int64_t grid_position(const Grid &g, int x, int y, in
 // and for BGK d*_i = (1 - lp) d_i + (w_i A + ...) +- (...), which keeps
 // lp = 0 (no collision) an exact identity.
 //
-// The d_i arrive multiplied by the storage scale s (a power of two: 1, or S
-// for F16S) and leave multiplied by it; the moments are unscaled exactly with
-// inv_s.  Returns rho - 1 and rho u_x (for the mass and flux reductions).
+// With SCALED the d_i arrive multiplied by the storage scale s (a power of
+// two, S for F16S) and leave multiplied by it; the moments are unscaled
+// exactly with inv_s.  Without it s and inv_s are ignored.  Returns rho - 1 and rho u_x (for the mass and flux reductions).
+// Rounded arithmetic that the compiler may neither contract nor reorder: a
+// node's collision then gives the same bits in every kernel it is inlined
+// into (one node per thread or several, any block shape), which keeps a
+// geometry's solve bit-identical alone and inside a batch.  Host code (the
+// per-launch constants) uses plain operators.
+template <typename T>
+struct Rn;
+template <>
+struct Rn<float> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+  static float add(float a, float b) { return a + b; }
+  static float sub(float a, float b) { return a - b; }
+  static float mul(float a, float b) { return a * b; }
+  static float fma(float a, float b, float c) { return a * b + c; }
+#endif
+};
+template <>
+struct Rn<double> {
+#ifdef __CUDA_ARCH__
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+#else
+  static double add(double a, double b) { return a + b; }
+  static double sub(double a, double b) { return a - b; }
+  static double mul(double a, double b) { return a * b; }
+  static double fma(double a, double b, double c) { return a * b + c; }
+#endif
+};
+
 // Per-launch constants of the collision, uniform over the nodes: filled once
 // on the host for a lattice's launches (kernel parameters, read by the node
 // arithmetic as constant operands), or per thread for a batch segment.
@@ -196,32 +232,33 @@ struct CollK {
 
 template <typename T>
 __host__ __device__ inline CollK<T> make_collk(T lp, T lm, T gx, T gy, T gz) {
+  using R = Rn<T>;
   CollK<T> K;
-  const T kp = T(1) - T(0.5) * lp, km = T(1) - T(0.5) * lm;
+  const T kp = R::fma(T(-0.5), lp, T(1)), km = R::fma(T(-0.5), lm, T(1));
   K.lp = lp;
-  K.om1 = T(1) - lp;
-  const T hp = T(0.5) * (T(1) - lp), hm = T(0.5) * (T(1) - lm);
-  K.al = hp + hm;
-  K.be = hp - hm;
-  K.q15 = T(1.5) * lp;
-  K.q3 = T(3) * kp;
+  K.om1 = R::sub(T(1), lp);
+  const T hp = R::mul(T(0.5), R::sub(T(1), lp)), hm = R::mul(T(0.5), R::sub(T(1), lm));
+  K.al = R::add(hp, hm);
+  K.be = R::sub(hp, hm);
+  K.q15 = R::mul(T(1.5), lp);
+  K.q3 = R::mul(T(3), kp);
   const T w[2] = {T(1) / T(18), T(1) / T(36)};
   for (int c = 0; c < 2; ++c) {
-    K.tp[c] = T(4.5) * lp * w[c];
-    K.tm[c] = T(3) * lm * w[c];
+    K.tp[c] = R::mul(R::mul(T(4.5), lp), w[c]);
+    K.tm[c] = R::mul(R::mul(T(3), lm), w[c]);
   }
   K.fp[0] = K.fm[0] = T(0);
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;
-    const T cg = T(CX(i)) * gx + T(CY(i)) * gy + T(CZ(i)) * gz;
+    const T cg = R::add(R::add(R::mul(T(CX(i)), gx), R::mul(T(CY(i)), gy)), R::mul(T(CZ(i)), gz));
     const T wi = i <= 6 ? w[0] : w[1];
-    K.fp[k] = T(9) * kp * wi * cg;
-    K.fm[k] = T(3) * km * wi * cg;
+    K.fp[k] = R::mul(R::mul(R::mul(T(9), kp), wi), cg);
+    K.fm[k] = R::mul(R::mul(R::mul(T(3), km), wi), cg);
   }
   K.g[0] = gx;
   K.g[1] = gy;
   K.g[2] = gz;
-  for (int a = 0; a < 3; ++a) K.hg[a] = T(0.5) * K.g[a];
+  for (int a = 0; a < 3; ++a) K.hg[a] = R::mul(T(0.5), K.g[a]);
   K.bgk = lm == lp;
   return K;
 }
@@ -235,67 +272,67 @@ __device__ __forceinline__ float recip<float>(float x) {
   return __fdividef(1.0f, x);  // rho is near 1: the fast reciprocal is well within FP32 parity
 }
 
-template <typename T, bool FORCE>
+template <typename T, bool FORCE, bool SCALED>
 __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
+  using R = Rn<T>;
   T sum[10], dif[10];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
-    sum[k] = d[2 * k - 1] + d[2 * k];
-    dif[k] = d[2 * k - 1] - d[2 * k];
+    sum[k] = R::add(d[2 * k - 1], d[2 * k]);
+    dif[k] = R::sub(d[2 * k - 1], d[2 * k]);
   }
-  const T sdrho = d[0] + (((sum[1] + sum[2]) + (sum[3] + sum[4])) + ((sum[5] + sum[6]) + (sum[7] + sum[8])) + sum[9]);
-  // pair k = (2k-1, 2k); velocity of the odd member
+  const T sdrho = R::add(d[0], R::add(R::add(R::add(R::add(sum[1], sum[2]), R::add(sum[3], sum[4])),
+                                             R::add(R::add(sum[5], sum[6]), R::add(sum[7], sum[8]))),
+                                      sum[9]));
+  // j = sum over pairs of c_(2k-1) (d_(2k-1) - d_(2k)), in ascending k
   T jx = 0, jy = 0, jz = 0;
+  bool fx = true, fy = true, fz = true;
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;
-    if (CX(i) == 1) jx += dif[k];
-    if (CX(i) == -1) jx -= dif[k];
-    if (CY(i) == 1) jy += dif[k];
-    if (CY(i) == -1) jy -= dif[k];
-    if (CZ(i) == 1) jz += dif[k];
-    if (CZ(i) == -1) jz -= dif[k];
+    if (CX(i)) { jx = fx ? (CX(i) > 0 ? dif[k] : -dif[k]) : (CX(i) > 0 ? R::add(jx, dif[k]) : R::sub(jx, dif[k])); fx = false; }
+    if (CY(i)) { jy = fy ? (CY(i) > 0 ? dif[k] : -dif[k]) : (CY(i) > 0 ? R::add(jy, dif[k]) : R::sub(jy, dif[k])); fy = false; }
+    if (CZ(i)) { jz = fz ? (CZ(i) > 0 ? dif[k] : -dif[k]) : (CZ(i) > 0 ? R::add(jz, dif[k]) : R::sub(jz, dif[k])); fz = false; }
   }
-  const T drho = sdrho * inv_s;
-  jx *= inv_s;
-  jy *= inv_s;
-  jz *= inv_s;
-  const T rho = T(1) + drho;
+  const T drho = SCALED ? R::mul(sdrho, inv_s) : sdrho;
+  if (SCALED) {
+    jx = R::mul(jx, inv_s);
+    jy = R::mul(jy, inv_s);
+    jz = R::mul(jz, inv_s);
+  }
+  const T rho = R::add(T(1), drho);
   const T inv = recip(rho);
   T ux, uy, uz;
   if (FORCE) {
-    ux = (jx + rho * K.hg[0]) * inv;
-    uy = (jy + rho * K.hg[1]) * inv;
-    uz = (jz + rho * K.hg[2]) * inv;
+    ux = R::mul(R::fma(rho, K.hg[0], jx), inv);
+    uy = R::mul(R::fma(rho, K.hg[1], jy), inv);
+    uz = R::mul(R::fma(rho, K.hg[2], jz), inv);
   } else {
-    ux = jx * inv;
-    uy = jy * inv;
-    uz = jz * inv;
+    ux = R::mul(jx, inv);
+    uy = R::mul(jy, inv);
+    uz = R::mul(jz, inv);
   }
   drho_out = drho;
-  rjx_out = rho * ux;
-  T q = K.q15 * (ux * ux + uy * uy + uz * uz);
-  if (FORCE) q += K.q3 * (ux * K.g[0] + uy * K.g[1] + uz * K.g[2]);
-  const T srho = s * rho;
-  const T sA = K.lp * sdrho - srho * q;  // s * A
-  d[0] = K.om1 * d[0] + T(WD(0)) * sA;
-  const T wsA[2] = {T(WD(1)) * sA, T(WD(7)) * sA};
+  rjx_out = R::mul(rho, ux);
+  T q = R::mul(K.q15, R::fma(uz, uz, R::fma(uy, uy, R::mul(ux, ux))));
+  if (FORCE) q = R::fma(K.q3, R::fma(uz, K.g[2], R::fma(uy, K.g[1], R::mul(ux, K.g[0]))), q);
+  const T srho = SCALED ? R::mul(s, rho) : rho;
+  const T sA = R::fma(-srho, q, R::mul(K.lp, sdrho));  // s * A
+  d[0] = R::fma(K.om1, d[0], R::mul(T(WD(0)), sA));
+  const T wsA[2] = {R::mul(T(WD(1)), sA), R::mul(T(WD(7)), sA)};
   // P = s (w_i A + rho (c.u)(...)), M = s rho (...) of pair k
   auto terms = [&](int k, T &P, T &M) {
     const int i = 2 * k - 1;
     const int c = i <= 6 ? 0 : 1;
     T cu = 0;
-    if (CX(i)) cu += T(CX(i)) * ux;
-    if (CY(i)) cu += T(CY(i)) * uy;
-    if (CZ(i)) cu += T(CZ(i)) * uz;
-    T tp = K.tp[c] * cu;
-    T tm = K.tm[c] * cu;
-    if (FORCE) {
-      tp += K.fp[k];
-      tm += K.fm[k];
-    }
-    P = wsA[c] + srho * (cu * tp);
-    M = srho * tm;
+    bool first = true;
+    if (CX(i)) { cu = CX(i) > 0 ? ux : -ux; first = false; }
+    if (CY(i)) { cu = first ? (CY(i) > 0 ? uy : -uy) : (CY(i) > 0 ? R::add(cu, uy) : R::sub(cu, uy)); first = false; }
+    if (CZ(i)) { cu = first ? (CZ(i) > 0 ? uz : -uz) : (CZ(i) > 0 ? R::add(cu, uz) : R::sub(cu, uz)); }
+    const T tp = FORCE ? R::fma(K.tp[c], cu, K.fp[k]) : R::mul(K.tp[c], cu);
+    const T tm = FORCE ? R::fma(K.tm[c], cu, K.fm[k]) : R::mul(K.tm[c], cu);
+    P = R::fma(srho, R::mul(cu, tp), wsA[c]);
+    M = R::mul(srho, tm);
   };
   if (K.bgk) {
 #pragma unroll
@@ -303,8 +340,8 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
       const int i = 2 * k - 1;
       T P, M;
       terms(k, P, M);
-      d[i] = K.om1 * d[i] + (P + M);
-      d[i + 1] = K.om1 * d[i + 1] + (P - M);
+      d[i] = R::fma(K.om1, d[i], R::add(P, M));
+      d[i + 1] = R::fma(K.om1, d[i + 1], R::sub(P, M));
     }
   } else {
     // a* +- b* with a = (d_i + d_opp)/2, b = (d_i - d_opp)/2 expanded, so
@@ -316,22 +353,19 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
       T P, M;
       terms(k, P, M);
       const T di = d[i], dj = d[i + 1];
-      d[i] = K.al * di + (K.be * dj + (P + M));
-      d[i + 1] = K.al * dj + (K.be * di + (P - M));
+      d[i] = R::fma(K.al, di, R::fma(K.be, dj, R::add(P, M)));
+      d[i + 1] = R::fma(K.al, dj, R::fma(K.be, di, R::sub(P, M)));
     }
   }
 }
 
 // The collision in the units a codec's step kernels load: S * d_i for F16S,
-// d_i otherwise (the scale is the literal 1 and folds away).
+// d_i otherwise.
 template <class C, bool FORCE>
 __device__ __forceinline__ void collide_stored(typename C::T (&d)[Q], const CollK<typename C::T> &K, float scale,
                                                float inv_scale, typename C::T &drho, typename C::T &rjx) {
   using T = typename C::T;
-  if constexpr (C::kScaled)
-    collide<T, FORCE>(d, K, T(scale), T(inv_scale), drho, rjx);
-  else
-    collide<T, FORCE>(d, K, T(1), T(1), drho, rjx);
+  collide<T, FORCE, C::kScaled>(d, K, T(scale), T(inv_scale), drho, rjx);
 }
 
 // ---------------------------------------------------------------------------

@@ -284,54 +284,66 @@ __device__ __forceinline__ bool et_linked(const IndirectNode &, const StepParams
 //   indirect: word k of the packed index (k = 0..8, direction 2k+1) holds the
 //             slot of x + c_{2k+1} in bits 0..30 (a ghost slot >= nfluid when
 //             that cell is solid) and in bit 31 whether x + c_{2k+2} is solid.
+// One node of the esoteric twist.  FAST (full grid only): the node has no
+// wall or solid link, so every position is the wrapped neighbour slot and no
+// store is redirected.
+template <bool FAST, class C, int AOS, bool IND, bool FORCE>
+__device__ __forceinline__ void et_node(const StepParams &p, NodeOf<IND> &nd, const Lattice<C, AOS> &A, double &m,
+                                        double &j) {
+  using T = typename C::T;
+  uint32_t w[10];  // packed index words (IDX addressing), kept across the collision
+  if (IND) {
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.ipad + nd.s);
+  }
+  T d[Q];
+  d[0] = A.ld(p.map[0], nd.s);
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    const int i = 2 * k - 1;
+    d[i] = A.ld(p.map[i], nd.s);
+    const int pos = IND ? (int)(w[k] & 0x7fffffffu) : et_pos(nd, p, i);
+    d[i + 1] = A.ld(p.map[i + 1], pos);
+  }
+  run_collision<C, FORCE>(d, p, m, j);
+  nd.launder_all();
+  if (IND) {
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)launder((int)w[k]);
+  }
+  A.st(p.map[0], nd.s, d[0]);
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    const int i = 2 * k - 1;
+    int pos;
+    bool lp, lm;
+    if (IND) {
+      pos = (int)(w[k] & 0x7fffffffu);
+      lp = pos < p.nfluid;
+      lm = (w[k] >> 31) == 0u;
+    } else {
+      pos = et_pos(nd, p, i);
+      lp = FAST || et_linked(nd, p, i);
+      lm = FAST || et_linked(nd, p, i + 1);
+    }
+    // odd direction i: to x + c_i; even direction i+1: to x itself
+    A.st(lp ? p.map[i + 1] : p.map[i], pos, d[i]);
+    A.st(lm ? p.map[i] : p.map[i + 1], nd.s, d[i + 1]);
+  }
+}
+
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS_IND k_et(StepParams p) {
-  using T = typename C::T;
   using Node = NodeOf<IND>;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
     Node nd;
     if (!nd.init_it(p, it)) continue;
-    uint32_t w[10];  // packed index words (IDX addressing), kept across the collision
-    if (IND) {
-#pragma unroll
-      for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.ipad + nd.s);
-    }
-    T d[Q];
-    d[0] = A.ld(p.map[0], nd.s);
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-      const int i = 2 * k - 1;
-      d[i] = A.ld(p.map[i], nd.s);
-      const int pos = IND ? (int)(w[k] & 0x7fffffffu) : et_pos(nd, p, i);
-      d[i + 1] = A.ld(p.map[i + 1], pos);
-    }
-    run_collision<C, FORCE>(d, p, m, j);
-    nd.launder_all();
-    if (IND) {
-#pragma unroll
-      for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)launder((int)w[k]);
-    }
-    A.st(p.map[0], nd.s, d[0]);
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-      const int i = 2 * k - 1;
-      int pos;
-      bool lp, lm;
-      if (IND) {
-        pos = (int)(w[k] & 0x7fffffffu);
-        lp = pos < p.nfluid;
-        lm = (w[k] >> 31) == 0u;
-      } else {
-        pos = et_pos(nd, p, i);
-        lp = et_linked(nd, p, i);
-        lm = et_linked(nd, p, i + 1);
-      }
-      // odd direction i: to x + c_i; even direction i+1: to x itself
-      A.st(lp ? p.map[i + 1] : p.map[i], pos, d[i]);
-      A.st(lm ? p.map[i] : p.map[i + 1], nd.s, d[i + 1]);
-    }
+    if (!IND && nd.fast)
+      et_node<true, C, AOS, IND, FORCE>(p, nd, A, m, j);
+    else
+      et_node<false, C, AOS, IND, FORCE>(p, nd, A, m, j);
   }
   if (RED) block_reduce_store(m, j, p.partials);
 }
