@@ -105,7 +105,9 @@ typedef struct lbm_config {
   int32_t store_hint;        /* LBM_OS_PUSH / LBM_OS_PULL, SoA: 1 = write the second lattice with
                                 cache-streaming (evict-first) stores, the GPU counterpart of the
                                 non-temporal stores of OS-NT (Sec. 3); 0 = ordinary stores */
-  int32_t reserved;          /* must be 0 */
+  int32_t tile_staging;      /* LBM_SWAP, full grid, SoA: 0 = stage each tile in shared memory with one
+                                tensor copy (TMA) when the row pitch is a multiple of 16 bytes,
+                                1 = plain loads */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */
@@ -123,7 +125,7 @@ typedef struct lbm_info {
   int32_t kernels_per_step;  /* launches one lbm_step(h, 1) makes */
   double f16_scale;          /* scale in use (LBM_F16S) */
   int32_t reduce_blocks;     /* blocks of the fused reduction */
-  int32_t reserved;
+  int32_t tile_staged;       /* 1 if the swap passes stage tiles with tensor copies */
 } lbm_info;
 
 typedef struct lbm lbm_t;
@@ -316,6 +318,17 @@ lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *be
 #define LBM_NOALLOC_CHUNK 65536
 lbm_status lbm_flux_noalloc(const void *f_dev, int32_t precision, int32_t layout, int64_t n, int64_t npad,
                             double f16_scale, double gx, double *out_dev, void *stream);
+
+/* Diagnostic, with no counterpart in the paper: the tile-staging kernels
+ * wait for their tensor copies with a time limit and record a timeout
+ * instead of spinning forever.  This call exercises that bounded wait on
+ * purpose: one GPU thread waits on a shared-memory barrier that nothing
+ * completes, for at most limit_ns nanoseconds (1000 .. 1e9).  Returns
+ * LBM_ERR_TIMEOUT when the wait gave up as designed (the expected result),
+ * LBM_OK if the barrier completed, LBM_ERR_INVALID_ARG for a limit out of
+ * range, LBM_ERR_CUDA on a runtime error.  stream: cudaStream_t or NULL;
+ * synchronises it. */
+lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, void *stream);
 
 #ifdef __cplusplus
 }

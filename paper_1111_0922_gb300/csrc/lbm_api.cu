@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -51,6 +52,11 @@ struct lbm {
   int32_t *d_cidx = nullptr;
   int64_t cg_nfirst = 0, cg_nlast = 0, cg_K = 0, cg_B = 0, cg_G = 0;
   int swap_tile[3] = {0, 0, 0};
+  // swap on a full grid: the lattice as a 4D tensor (x, y, z, array) for the
+  // tile-staging tensor copies, when the layout allows them
+  alignas(64) CUtensorMap swap_map{};
+  bool swap_tma = false;
+  int nsm = 0;
 };
 
 static std::string g_last_error;
@@ -73,6 +79,24 @@ static lbm_status fail(lbm_t *h, lbm_status s, const char *fmt, ...) {
     cudaError_t e_ = (call);                                                                       \
     if (e_ != cudaSuccess) return fail(h, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links only the runtime).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
 
 static lbm_status check_launch(lbm_t *h, const char *what) {
   cudaError_t e = cudaGetLastError();
@@ -345,7 +369,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
   if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint = 1 needs LBM_OS_PUSH or LBM_OS_PULL with LBM_SOA");
-  if (cfg->reserved != 0) return fail(nullptr, LBM_ERR_INVALID_ARG, "reserved must be 0");
+  if (cfg->tile_staging != 0 && cfg->tile_staging != 1)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "tile_staging must be 0 or 1");
 
   lbm_t *h = new lbm_t();
   h->cfg = *cfg;
@@ -390,6 +415,7 @@ lbm_status lbm_sync(lbm_t *h) {
   int flags[4];
   CUDA_TRY(h, cudaMemcpy(flags, h->d_err, sizeof flags, cudaMemcpyDeviceToHost));
   if (flags[0]) return fail(h, LBM_ERR_BOUNDS, "a kernel bounds check tripped (code %d)", flags[0]);
+  if (flags[1]) return fail(h, LBM_ERR_TIMEOUT, "a kernel's bounded wait for a tile copy gave up");
   return LBM_OK;
 }
 
@@ -533,6 +559,33 @@ static lbm_status build_geometry(lbm_t *h) {
     if (st != LBM_OK) return st;
     h->idx_folded = true;
   }
+  h->swap_tma = false;
+  if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA && c.tile_staging == 0) {
+    // tensor copies need 16-byte row pitches and inner box extents
+    const SwapTiles t = swap_tiles(h);
+    const cuuint64_t es = (cuuint64_t)store_size(c.precision);
+    EncodeTiledFn enc = encode_tiled();
+    if (enc && (h->grid.sx * (int64_t)es) % 16 == 0 && ((int64_t)t.tx * (int64_t)es) % 16 == 0 && h->grid.hx == 0 &&
+        h->grid.hy == 0 && h->grid.hz == 0 && h->grid.zoff == 0) {
+      const cuuint64_t dims[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)c.nz, (cuuint64_t)Q};
+      const cuuint64_t strides[3] = {(cuuint64_t)h->grid.sx * es, (cuuint64_t)h->grid.sxy * es,
+                                     (cuuint64_t)h->npad * es};
+      const cuuint32_t box[4] = {(cuuint32_t)t.tx, (cuuint32_t)t.ty, (cuuint32_t)t.tz, (cuuint32_t)Q};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      const CUtensorMapDataType dt = c.precision == LBM_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                     : c.precision == LBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+      const CUresult r = enc(&h->swap_map, dt, 4, h->d_A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      h->swap_tma = r == CUDA_SUCCESS;
+    }
+    if (h->swap_tma && h->nsm == 0) {
+      int nsm = 0;
+      CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+      h->nsm = nsm;
+    }
+  }
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
   int64_t need = std::max<int64_t>(blocks_of(L), reduce_blocks_for(h->nn));
@@ -563,6 +616,7 @@ static void reset_geometry(lbm_t *h) {
   h->cells = (int64_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
   h->nodes = h->nghost = h->nn = h->slots = h->npad = h->ipad = 0;
   h->idx_folded = false;
+  h->swap_tma = false;
   h->steps = 0;
   for (int i = 0; i < Q; ++i) h->map[i] = i;
 }
@@ -700,6 +754,7 @@ lbm_status lbm_get_info(const lbm_t *h, lbm_info *info) {
   info->kernels_per_step = kernels_per_step(h);
   info->f16_scale = h->scale;
   info->reduce_blocks = h->partial_blocks;
+  info->tile_staged = h->swap_tma ? 1 : 0;
   return LBM_OK;
 }
 
@@ -963,8 +1018,13 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
   for (int c = 0; c < t.ncolours; ++c) {
     t.colour = c;
     p.partials = h->d_partials + 2 * used;
-    launch_swap_pass(p, t, k, h->stream);
-    used += swap_blocks(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2], c);
+    if (h->swap_tma) {
+      // two persistent blocks per SM (the kernel's register budget)
+      used += launch_swap_pass_tma(p, t, k, &h->swap_map, 2 * h->nsm, h->stream);
+    } else {
+      launch_swap_pass(p, t, k, h->stream);
+      used += swap_blocks(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2], c);
+    }
   }
   if (red_blocks) *red_blocks = used;
   return LBM_OK;

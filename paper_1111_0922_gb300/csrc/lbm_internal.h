@@ -2,6 +2,7 @@
 // selection keys, launch shapes, and the launchers each .cu file exports.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -69,6 +70,13 @@ struct SwapTiles {
   int ncolours;
 };
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
+// the same pass with tensor-copy staging (full grid, SoA, strides multiple of
+// 16 bytes); `map` describes the lattice as a 4D tensor (x, y, z, array) with
+// the tile as its box.  Launches at most max_blocks persistent blocks and
+// returns how many it launched.
+int launch_swap_pass_tma(const StepParams &p, const SwapTiles &t, const KernelKey &k, const CUtensorMap *map,
+                         int max_blocks, cudaStream_t s);
+size_t swap_tma_smem_bytes(int tile_cells, size_t stored, size_t computed);
 size_t swap_smem_bytes(const SwapTiles &t, int precision);
 int swap_colours(const SwapTiles &t, int px, int py, int pz);
 // node lists: link exchanges after a collide-into-reversed-slots pass

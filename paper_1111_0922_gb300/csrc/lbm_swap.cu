@@ -15,8 +15,11 @@
 // are completed there; a link to a tile of an earlier colour is completed by
 // exchanging with global memory (that tile left its end reversed); a link to a
 // tile of a later colour is left reversed for that tile to complete.
+#include <cuda.h>
+
 #include <algorithm>
 
+#include "../../include/lbm.h"
 #include "lbm_dispatch.cuh"
 #include "lbm_internal.h"
 
@@ -39,51 +42,55 @@ __device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
-// One pass: the tiles of one colour.  Thread (lx, ly, lz) of the block owns
-// cell org + (lx, ly, lz) of its tile.
-template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp) {
+// Classify the 26 neighbouring tiles of `tile` for this pass: bit
+// tile_bit(o) of *em is set when the neighbour at offset o has an earlier
+// colour, of *sm when the tile is its own neighbour across a periodic face.
+__device__ __forceinline__ void classify_tiles(const Grid &g, const SwapPass &sp, const int tile[3], unsigned &em,
+                                               unsigned &sm) {
+  const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
+  const int per[3] = {g.px, g.py, g.pz};
+  em = 0;
+  sm = 0;
+  for (int oz = -1; oz <= 1; ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int o[3] = {ox, oy, oz};
+        int nb[3];
+        bool exists = true;
+        for (int a = 0; a < 3; ++a) {
+          nb[a] = tile[a] + o[a];
+          if (nb[a] < 0 || nb[a] >= nt[a]) {
+            if (!per[a]) exists = false;
+            nb[a] = (nb[a] + nt[a]) % nt[a];
+          }
+        }
+        if (!exists) continue;
+        if (nb[0] == tile[0] && nb[1] == tile[1] && nb[2] == tile[2]) {
+          sm |= 1u << tile_bit(ox, oy, oz);
+          continue;
+        }
+        const int col = axis_colour(nb[0], nt[0], per[0]) +
+                        sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
+        if (col < sp.colour) em |= 1u << tile_bit(ox, oy, oz);
+      }
+}
+
+// One tile, all threads of the block (thread (lx, ly, lz) owns cell
+// org + (lx, ly, lz)).  Phase 1: every node collides; its post-collision
+// PDFs go to S[i * TN + t] (S in shared memory).  The node's stored PDFs
+// come from global memory, or from `stage` (the tile as the tensor copy left
+// it in shared memory, same layout; it may alias S).  Phase 2: each node
+// gathers the PDFs that end in its slots and writes them, and completes its
+// links to tiles of earlier colours in global memory.
+template <class C, int AOS, bool FORCE>
+__device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
+                                          const typename C::S *stage, const int org[3], unsigned em, unsigned sm,
+                                          double &m, double &jsum) {
   using T = typename C::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *S = reinterpret_cast<T *>(smem_raw);
-  __shared__ unsigned earlier_mask, self_mask;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const Grid &g = p.g;
   const int TN = sp.tx * sp.ty * sp.tz;
-  const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
-                       sp.start[2] + 2 * (int)blockIdx.z};
-  const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
   const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  if (t == 0) {
-    // classify the 26 neighbouring tiles once per block
-    const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
-    const int per[3] = {g.px, g.py, g.pz};
-    unsigned em = 0, sm = 0;
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-          const int o[3] = {ox, oy, oz};
-          int nb[3];
-          bool exists = true;
-          for (int a = 0; a < 3; ++a) {
-            nb[a] = tile[a] + o[a];
-            if (nb[a] < 0 || nb[a] >= nt[a]) {
-              if (!per[a]) exists = false;
-              nb[a] = (nb[a] + nt[a]) % nt[a];
-            }
-          }
-          if (!exists) continue;
-          if (nb[0] == tile[0] && nb[1] == tile[1] && nb[2] == tile[2]) {
-            sm |= 1u << tile_bit(ox, oy, oz);
-            continue;
-          }
-          const int col = axis_colour(nb[0], nt[0], per[0]) +
-                          sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
-          if (col < sp.colour) em |= 1u << tile_bit(ox, oy, oz);
-        }
-    earlier_mask = em;
-    self_mask = sm;
-  }
   const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
   // extent of this tile inside the box (the last tile of an axis may be cut)
   const int ex = min(sp.tx, g.nx - org[0]), ey = min(sp.ty, g.ny - org[1]), ez = min(sp.tz, g.nz - org[2]);
@@ -95,15 +102,19 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
     nd.z = org[2] + lz;
     active = nd.setup(g);
   }
-  double m = 0.0, jsum = 0.0;
   if (active) {
     T d[Q];
+    if (stage) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
+      for (int i = 0; i < Q; ++i) d[i] = C::raw(stage[i * TN + t]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
+    }
     T drho, rjx;
     collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
-    m = 1.0 + (double)drho;
-    jsum = (double)rjx;
+    m += 1.0 + (double)drho;
+    jsum += (double)rjx;
 #pragma unroll
     for (int i = 0; i < Q; ++i) S[i * TN + t] = d[i];
   }
@@ -112,7 +123,6 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
     // Gather every incoming value first (the loads from earlier tiles are
     // independent and overlap), then write: the remote slots written below
     // belong to earlier tiles and are never read by this pass again.
-    const unsigned em = earlier_mask, sm = self_mask;
     T v[Q];
     int remote[Q];
     v[0] = S[t];
@@ -157,6 +167,160 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
       if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
     }
   }
+}
+
+// One pass: the tiles of one colour, one block per tile.
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp) {
+  using T = typename C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);
+  __shared__ unsigned earlier_mask, self_mask;
+  const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
+                       sp.start[2] + 2 * (int)blockIdx.z};
+  const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    unsigned em, sm;
+    classify_tiles(p.g, sp, tile, em, sm);
+    earlier_mask = em;
+    self_mask = sm;
+  }
+  __syncthreads();
+  double m = 0.0, jsum = 0.0;
+  swap_tile<C, AOS, FORCE>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
+  if (RED) block_reduce_store(m, jsum, p.partials);
+}
+
+// ---------------------------------------------------------------------------
+// The same pass with the tiles staged by the tensor memory accelerator: a
+// persistent block walks its share of the pass's tiles and, while it works
+// on one tile, the tensor copy of its next tile (all 19 arrays of the tile's
+// box in one 4D copy: x, y, z, array) is already in flight into the other of
+// two shared-memory buffers.  Every wait on a copy is bounded by a time
+// limit; on expiry the block records the timeout and stops.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// true when the phase with the given parity has completed before limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t a = smem_addr(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr uint64_t kTmaWaitNs = 1000000000ull;  // 1 s
+
+// Self-test of the bounded wait: one thread waits on a barrier that expects
+// one arrival which never comes.
+__device__ int g_wait_selftest;
+__global__ void k_wait_selftest(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  g_wait_selftest = mbar_wait(&bar, 0, limit_ns) ? 1 : 2;
+}
+
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, 2) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
+  using T = typename C::T;
+  using S = typename C::S;
+  constexpr bool kInPlace = sizeof(T) == sizeof(S);  // F32, F64: collide into the staged buffer
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ unsigned masks[2];
+  const int TN = sp.tx * sp.ty * sp.tz;
+  const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
+  const size_t stage_pad = (stage_bytes + 127) / 128 * 128;
+  // tensor-copy destinations on 128-byte boundaries (the launch adds 128
+  // bytes of slack for this)
+  unsigned char *base = smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u);
+  S *stage[2] = {reinterpret_cast<S *>(base), reinterpret_cast<S *>(base + stage_pad)};
+  T *Sx = reinterpret_cast<T *>(base + 2 * stage_pad);  // separate buffer when not in place
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int ntiles = sp.count[0] * sp.count[1] * sp.count[2];
+  auto tile_of = [&](int n, int tile[3]) {
+    tile[0] = sp.start[0] + 2 * (n % sp.count[0]);
+    tile[1] = sp.start[1] + 2 * ((n / sp.count[0]) % sp.count[1]);
+    tile[2] = sp.start[2] + 2 * (n / (sp.count[0] * sp.count[1]));
+  };
+  auto issue = [&](int n, int b) {
+    int tile[3];
+    tile_of(n, tile);
+    mbar_expect_tx(&bar[b], (uint32_t)stage_bytes);
+    tma_load_4d(stage[b], &map, tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz, 0, &bar[b]);
+  };
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  double m = 0.0, jsum = 0.0;
+  const int G = gridDim.x;
+  if (t == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int it = 0;
+  for (int n = blockIdx.x; n < ntiles; n += G, ++it) {
+    const int b = it & 1;
+    int tile[3];
+    tile_of(n, tile);
+    if (t == 0) {
+      // the other buffer was last read in the previous iteration, which
+      // ended with a block barrier; order those generic-proxy accesses
+      // before the tensor copy overwrites it
+      if (n + G < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(n + G, b ^ 1);
+      }
+      unsigned em, sm;
+      classify_tiles(p.g, sp, tile, em, sm);
+      masks[0] = em;
+      masks[1] = sm;
+    }
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(p.err + 1, 1);
+        // let the copies still in flight land before the block exits
+        mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
+        if (n + G < ntiles) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitNs);
+      }
+      break;
+    }
+    const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
+    T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
+    swap_tile<C, 0, FORCE>(p, sp, Sbuf, stage[b], org, masks[0], masks[1], m, jsum);
+    __syncthreads();
+  }
   if (RED) block_reduce_store(m, jsum, p.partials);
 }
 
@@ -166,6 +330,18 @@ struct LaunchSwap {
     auto k = k_swap_pass<C, AOS, false, FORCE, RED>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp);
+  }
+};
+
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+struct LaunchSwapTma {
+  static void run(const StepParams &p, const SwapPass &sp, const CUtensorMap *map, int grid, cudaStream_t s) {
+    if constexpr (AOS == 0 && !IND) {
+      auto k = k_swap_tma<C, FORCE, RED>;
+      const size_t smem = swap_tma_smem_bytes(sp.tx * sp.ty * sp.tz, sizeof(typename C::S), sizeof(typename C::T));
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<grid, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp, *map);
+    }
   }
 };
 
@@ -194,7 +370,7 @@ static void axis_set(int nt, int periodic, int colour, int &start, int &count) {
   count = colour < nt ? (nt - colour + 1) / 2 : 0;
 }
 
-void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s) {
+static SwapPass pass_of(const StepParams &p, const SwapTiles &t) {
   SwapPass sp;
   sp.tx = t.tx;
   sp.ty = t.ty;
@@ -211,9 +387,29 @@ void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &
   axis_set(t.ntx, p.g.px, c0, sp.start[0], sp.count[0]);
   axis_set(t.nty, p.g.py, c1, sp.start[1], sp.count[1]);
   axis_set(t.ntz, p.g.pz, c2, sp.start[2], sp.count[2]);
+  return sp;
+}
+
+void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s) {
+  const SwapPass sp = pass_of(p, t);
   if (sp.count[0] * sp.count[1] * sp.count[2] == 0) return;
   const dim3 blocks(sp.count[0], sp.count[1], sp.count[2]);
   dispatch<LaunchSwap>(k.precision, k.aos, false, k.force, k.red, p, sp, swap_smem_bytes(t, k.precision), blocks, s);
+}
+
+int launch_swap_pass_tma(const StepParams &p, const SwapTiles &t, const KernelKey &k, const CUtensorMap *map,
+                         int max_blocks, cudaStream_t s) {
+  const SwapPass sp = pass_of(p, t);
+  const int ntiles = sp.count[0] * sp.count[1] * sp.count[2];
+  if (ntiles == 0) return 0;
+  const int grid = std::min(ntiles, max_blocks);
+  dispatch<LaunchSwapTma>(k.precision, 0, false, k.force, k.red, p, sp, map, grid, s);
+  return grid;
+}
+
+size_t swap_tma_smem_bytes(int tile_cells, size_t stored, size_t computed) {
+  const size_t stage = ((size_t)Q * tile_cells * stored + 127) / 128 * 128;
+  return 128 + 2 * stage + (stored == computed ? 0 : (size_t)Q * tile_cells * computed);
 }
 
 int swap_colours(const SwapTiles &t, int px, int py, int pz) {
@@ -282,3 +478,18 @@ void launch_swap_links(const StepParams &p, int precision, int aos, cudaStream_t
 }
 
 }  // namespace lbmk
+
+extern "C" lbm_status lbm_selftest_bounded_wait(int64_t limit_ns, void *stream) {
+  if (limit_ns < 1000 || limit_ns > 1000000000) return LBM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int zero = 0;
+  if (cudaMemcpyToSymbolAsync(lbmk::g_wait_selftest, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  lbmk::k_wait_selftest<<<1, 1, 0, s>>>((uint64_t)limit_ns);
+  int r = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(&r, lbmk::g_wait_selftest, sizeof r, 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  return r == 2 ? LBM_ERR_TIMEOUT : (r == 1 ? LBM_OK : LBM_ERR_CUDA);
+}

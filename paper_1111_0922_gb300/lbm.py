@@ -45,7 +45,7 @@ class lbm_config(ctypes.Structure):
                 ("f16_scale", ctypes.c_double), ("trt_magic", ctypes.c_double),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("cg_shift", ctypes.c_int32), ("pair_x", ctypes.c_int32),
-                ("store_hint", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("store_hint", ctypes.c_int32), ("tile_staging", ctypes.c_int32),
                 ("stream", ctypes.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
@@ -56,7 +56,7 @@ class lbm_info(ctypes.Structure):
                 ("index_bytes", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("natural", ctypes.c_int32), ("kernels_per_step", ctypes.c_int32),
                 ("f16_scale", ctypes.c_double), ("reduce_blocks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("tile_staged", ctypes.c_int32)]
 
 
 class lbm_batch_config(ctypes.Structure):
@@ -118,6 +118,7 @@ SIGNATURES = {
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "lbm_flux_noalloc": (_I, [_P, ctypes.c_int32, ctypes.c_int32, _I64, _I64, ctypes.c_double,
                               ctypes.c_double, _P, _P]),
+    "lbm_selftest_bounded_wait": (_I, [_I64, _P]),
 }
 
 _lib = None
@@ -288,6 +289,12 @@ def lbm_flux_noalloc(f_dev, precision, layout, n, npad, f16_scale, gx, out_dev, 
         raise LBMError(st, "lbm_flux_noalloc rejected the call")
 
 
+def lbm_selftest_bounded_wait(limit_ns, stream=None):
+    """Run the bounded-wait self-test; returns the status (LBM_ERR_TIMEOUT is
+    the expected result: the wait gave up after limit_ns)."""
+    return int(load().lbm_selftest_bounded_wait(int(limit_ns), ctypes.c_void_p(int(stream) if stream else 0)))
+
+
 # ---------------------------------------------------------------------------
 # Convenience object over the same calls
 
@@ -320,7 +327,7 @@ class Lattice:
     def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
                  layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
                  f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0, pair_x=0,
-                 trt_magic=0.0, store_hint=0, stream=None, use_torch_allocator=True):
+                 trt_magic=0.0, store_hint=0, tile_staging=0, stream=None, use_torch_allocator=True):
         self.cfg = lbm_config_default()
         c = self.cfg
         c.nx, c.ny, c.nz = (int(d) for d in dims)
@@ -340,6 +347,7 @@ class Lattice:
         c.cg_shift = int(cg_shift)
         c.pair_x = int(pair_x)
         c.store_hint = int(store_hint)
+        c.tile_staging = int(tile_staging)
         self._alloc = None
         if stream is None or use_torch_allocator:
             import torch
