@@ -294,8 +294,8 @@ def run_sweep(torch, lbm, args, hbm):
                     steps = args.sweep_steps
                     total, per = timed_steps(torch, lat, steps, per_launch=False)
                     mflups = n * steps / total / 1e6
-                    roof = model.roof_mflups(variant, False, precision, hbm)
-                    out[key] = {"mflups": round(mflups, 1), "roof_mflups": round(roof, 1),
+                    bound, roof = model.bound_roof(variant, False, precision, hbm)
+                    out[key] = {"mflups": round(mflups, 1), "bound": bound, "roof_mflups": round(roof, 1),
                                 "frac": round(mflups / roof, 4),
                                 "bytes_per_flup": model.gpu_bytes(variant, False, precision),
                                 "kernels_per_step": lat.info.kernels_per_step}
@@ -394,8 +394,10 @@ def run_paper_shapes(torch, lbm, args, hbm):
                 n = int(lat.info.nodes)
                 mflups = n * args.shape_steps / total / 1e6
                 roof = model.roof_mflups(variant, True, precision, hbm)
+                bound, broof = model.bound_roof(variant, True, precision, hbm, force=True, trt=True)
                 out["%s/%s/%s" % (name, variant, precision)] = {
-                    "fluid_nodes": n, "mflups": round(mflups, 1), "frac_of_hbm_roof": round(mflups / roof, 4)}
+                    "fluid_nodes": n, "mflups": round(mflups, 1), "frac_of_hbm_roof": round(mflups / roof, 4),
+                    "bound": bound, "frac": round(mflups / broof, 4)}
                 lat.close()
                 torch.cuda.empty_cache()
     log("paper_shapes", out)

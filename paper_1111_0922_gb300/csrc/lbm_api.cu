@@ -1019,8 +1019,7 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
     t.colour = c;
     p.partials = h->d_partials + 2 * used;
     if (h->swap_tma) {
-      // two persistent blocks per SM (the kernel's register budget)
-      used += launch_swap_pass_tma(p, t, k, &h->swap_map, 2 * h->nsm, h->stream);
+      used += launch_swap_pass_tma(p, t, k, &h->swap_map, h->nsm, h->stream);
     } else {
       launch_swap_pass(p, t, k, h->stream);
       used += swap_blocks(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2], c);

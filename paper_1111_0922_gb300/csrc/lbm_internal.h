@@ -72,10 +72,10 @@ struct SwapTiles {
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
 // the same pass with tensor-copy staging (full grid, SoA, strides multiple of
 // 16 bytes); `map` describes the lattice as a 4D tensor (x, y, z, array) with
-// the tile as its box.  Launches at most max_blocks persistent blocks and
-// returns how many it launched.
+// the tile as its box.  Launches persistent blocks (as many as are resident
+// at once on nsm SMs, at most one per tile) and returns how many.
 int launch_swap_pass_tma(const StepParams &p, const SwapTiles &t, const KernelKey &k, const CUtensorMap *map,
-                         int max_blocks, cudaStream_t s);
+                         int nsm, cudaStream_t s);
 size_t swap_tma_smem_bytes(int tile_cells, size_t stored, size_t computed);
 size_t swap_smem_bytes(const SwapTiles &t, int precision);
 int swap_colours(const SwapTiles &t, int px, int py, int pz);

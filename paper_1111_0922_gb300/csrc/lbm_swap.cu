@@ -42,37 +42,42 @@ __device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
-// Classify the 26 neighbouring tiles of `tile` for this pass: bit
-// tile_bit(o) of *em is set when the neighbour at offset o has an earlier
-// colour, of *sm when the tile is its own neighbour across a periodic face.
-__device__ __forceinline__ void classify_tiles(const Grid &g, const SwapPass &sp, const int tile[3], unsigned &em,
-                                               unsigned &sm) {
+// Classify one of the 27 tile offsets l (o = (l%3 - 1, (l/3)%3 - 1, l/9 - 1),
+// so l = tile_bit(o)) of `tile` for this pass: `earlier` when that neighbour
+// exists and has an earlier colour, `self` when the tile is its own neighbour
+// across a periodic face.  The threads of a block take the offsets in
+// parallel and OR the bits together in shared memory.
+__device__ __forceinline__ void classify_offset(const Grid &g, const SwapPass &sp, const int tile[3], int l,
+                                                bool &earlier, bool &self) {
+  const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, l / 9 - 1};
   const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
   const int per[3] = {g.px, g.py, g.pz};
-  em = 0;
-  sm = 0;
-  for (int oz = -1; oz <= 1; ++oz)
-    for (int oy = -1; oy <= 1; ++oy)
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int o[3] = {ox, oy, oz};
-        int nb[3];
-        bool exists = true;
-        for (int a = 0; a < 3; ++a) {
-          nb[a] = tile[a] + o[a];
-          if (nb[a] < 0 || nb[a] >= nt[a]) {
-            if (!per[a]) exists = false;
-            nb[a] = (nb[a] + nt[a]) % nt[a];
-          }
-        }
-        if (!exists) continue;
-        if (nb[0] == tile[0] && nb[1] == tile[1] && nb[2] == tile[2]) {
-          sm |= 1u << tile_bit(ox, oy, oz);
-          continue;
-        }
-        const int col = axis_colour(nb[0], nt[0], per[0]) +
-                        sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
-        if (col < sp.colour) em |= 1u << tile_bit(ox, oy, oz);
-      }
+  bool exists = true;
+  self = true;
+  int nb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nb[a] = tile[a] + o[a];
+    if (nb[a] < 0 || nb[a] >= nt[a]) {
+      if (!per[a]) exists = false;
+      nb[a] = (nb[a] + nt[a]) % nt[a];
+    }
+    self = self && nb[a] == tile[a];
+  }
+  const int col = axis_colour(nb[0], nt[0], per[0]) +
+                  sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
+  earlier = exists && !self && col < sp.colour;
+  self = exists && self;
+}
+
+__device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp, const int tile[3], int t, int nthreads,
+                                              unsigned *em, unsigned *sm) {
+  for (int l = t; l < 27; l += nthreads) {
+    bool e, f;
+    classify_offset(g, sp, tile, l, e, f);
+    if (e) atomicOr(em, 1u << l);
+    if (f) atomicOr(sm, 1u << l);
+  }
 }
 
 // One tile, all threads of the block (thread (lx, ly, lz) owns cell
@@ -134,12 +139,15 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
       const bool in_x = dx == 0 || (dx < 0 ? lx > 0 : lx < ex - 1);
       const bool in_y = dy == 0 || (dy < 0 ? ly > 0 : ly < ey - 1);
       const bool in_z = dz == 0 || (dz < 0 ? lz > 0 : lz < ez - 1);
-      // source slot, or -1 across a wall or from a solid cell (the fast path
-      // has neither: walls lie on tile faces and there is no solid cell)
-      const int src = nd.fast ? nd.nb_fast(p, OPP(i)) : nd.nb(p, OPP(i));
-      if (src < 0) {
-        v[i] = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
-        continue;
+      // source slot, or -1 across a wall or from a solid cell (a fast node
+      // has neither, and needs the slot only for a remote exchange)
+      int src = 0;
+      if (!nd.fast) {
+        src = nd.nb(p, OPP(i));
+        if (src < 0) {
+          v[i] = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
+          continue;
+        }
       }
       if (in_x && in_y && in_z) {
         v[i] = S[i * TN + t + dx + sp.tx * (dy + sp.ty * dz)];  // inside the tile
@@ -154,6 +162,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         v[i] = S[i * TN + wx + sp.tx * (wy + sp.ty * wz)];
       } else if (em & (1u << bit)) {
         // earlier tile: its reversed slot holds the PDF for us; ours goes there
+        if (nd.fast) src = nd.nb_fast(p, OPP(i));
         remote[i] = src;
         v[i] = L.ld(OPP(i), src);
       } else {
@@ -171,7 +180,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
 
 // One pass: the tiles of one colour, one block per tile.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
-__global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp) {
+__global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, SwapPass sp) {
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);
@@ -179,12 +188,10 @@ __global__ void __launch_bounds__(256, 2) k_swap_pass(StepParams p, SwapPass sp)
   const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
                        sp.start[2] + 2 * (int)blockIdx.z};
   const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
-  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
-    unsigned em, sm;
-    classify_tiles(p.g, sp, tile, em, sm);
-    earlier_mask = em;
-    self_mask = sm;
-  }
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (t == 0) earlier_mask = self_mask = 0u;
+  __syncthreads();
+  classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
   __syncthreads();
   double m = 0.0, jsum = 0.0;
   swap_tile<C, AOS, FORCE>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
@@ -251,13 +258,13 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
 }
 
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(256, 2) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
+__global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
   using T = typename C::T;
   using S = typename C::S;
   constexpr bool kInPlace = sizeof(T) == sizeof(S);  // F32, F64: collide into the staged buffer
   extern __shared__ __align__(128) unsigned char smem_tma[];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ unsigned masks[2];
+  __shared__ unsigned masks[2][2];  // [buffer][earlier, self]
   const int TN = sp.tx * sp.ty * sp.tz;
   const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
   const size_t stage_pad = (stage_bytes + 127) / 128 * 128;
@@ -283,6 +290,7 @@ __global__ void __launch_bounds__(256, 2) k_swap_tma(StepParams p, SwapPass sp, 
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    masks[0][0] = masks[0][1] = masks[1][0] = masks[1][1] = 0u;
   }
   __syncthreads();
   double m = 0.0, jsum = 0.0;
@@ -301,11 +309,9 @@ __global__ void __launch_bounds__(256, 2) k_swap_tma(StepParams p, SwapPass sp, 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(n + G, b ^ 1);
       }
-      unsigned em, sm;
-      classify_tiles(p.g, sp, tile, em, sm);
-      masks[0] = em;
-      masks[1] = sm;
     }
+    // (the bits of this buffer were cleared when it was last used)
+    classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &masks[b][0], &masks[b][1]);
     const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
@@ -318,7 +324,10 @@ __global__ void __launch_bounds__(256, 2) k_swap_tma(StepParams p, SwapPass sp, 
     }
     const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
     T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
-    swap_tile<C, 0, FORCE>(p, sp, Sbuf, stage[b], org, masks[0], masks[1], m, jsum);
+    const unsigned em = masks[b][0], sm = masks[b][1];
+    swap_tile<C, 0, FORCE>(p, sp, Sbuf, stage[b], org, em, sm, m, jsum);
+    // every thread read this buffer's bits before the barrier inside swap_tile
+    if (t == 0) masks[b][0] = masks[b][1] = 0u;
     __syncthreads();
   }
   if (RED) block_reduce_store(m, jsum, p.partials);
@@ -333,14 +342,25 @@ struct LaunchSwap {
   }
 };
 
+// Persistent launch: as many blocks as fit on the GPU at once (resident
+// blocks per SM for this block shape and shared memory x SMs), at most one
+// per tile.  Returns the number of blocks launched.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchSwapTma {
-  static void run(const StepParams &p, const SwapPass &sp, const CUtensorMap *map, int grid, cudaStream_t s) {
+  static void run(const StepParams &p, const SwapPass &sp, const CUtensorMap *map, int nsm, int ntiles,
+                  cudaStream_t s, int *launched) {
+    *launched = 0;
     if constexpr (AOS == 0 && !IND) {
       auto k = k_swap_tma<C, FORCE, RED>;
-      const size_t smem = swap_tma_smem_bytes(sp.tx * sp.ty * sp.tz, sizeof(typename C::S), sizeof(typename C::T));
+      const int threads = sp.tx * sp.ty * sp.tz;
+      const size_t smem = swap_tma_smem_bytes(threads, sizeof(typename C::S), sizeof(typename C::T));
       if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+      const int grid = std::min(ntiles, per_sm * std::max(nsm, 1));
       k<<<grid, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp, *map);
+      *launched = grid;
     }
   }
 };
@@ -398,13 +418,13 @@ void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &
 }
 
 int launch_swap_pass_tma(const StepParams &p, const SwapTiles &t, const KernelKey &k, const CUtensorMap *map,
-                         int max_blocks, cudaStream_t s) {
+                         int nsm, cudaStream_t s) {
   const SwapPass sp = pass_of(p, t);
   const int ntiles = sp.count[0] * sp.count[1] * sp.count[2];
   if (ntiles == 0) return 0;
-  const int grid = std::min(ntiles, max_blocks);
-  dispatch<LaunchSwapTma>(k.precision, 0, false, k.force, k.red, p, sp, map, grid, s);
-  return grid;
+  int launched = 0;
+  dispatch<LaunchSwapTma>(k.precision, 0, false, k.force, k.red, p, sp, map, nsm, ntiles, s, &launched);
+  return launched;
 }
 
 size_t swap_tma_smem_bytes(int tile_cells, size_t stored, size_t computed) {

@@ -83,6 +83,39 @@ def roof_mflups(variant: str, indirect: bool, precision: str, hbm_gbs: float) ->
     return hbm_gbs * 1e9 / gpu_bytes(variant, indirect, precision) / 1e6
 
 
+# FP64 instruction roof on GB300: 2 FP64 thread-instructions per clock per SM
+# (ncu's sm__sass_thread_inst_executed_op_dfma_pred_on peak) on 152 SMs at the
+# 2.07 GHz maximum SM clock.  The BGK collision issues about 143 FP64
+# instructions per update without a body force (ncu, AA pattern on 256^3);
+# counted from the source, a force adds 7 (u, u.g) and TRT adds 18 (two more
+# operations per opposite pair).
+FP64_INST_PER_CLK_SM = 2
+GB300_SMS = 152
+GB300_SM_GHZ = 2.07
+FP64_INST_BGK = 143
+
+
+def fp64_inst_per_flup(force: bool = False, trt: bool = False) -> int:
+    return FP64_INST_BGK + (7 if force else 0) + (18 if trt else 0)
+
+
+def fp64_roof_mflups(force: bool = False, trt: bool = False) -> float:
+    """FP64-pipe roofline in MFLUP/s of an FP64 step (any scheme)."""
+    rate = FP64_INST_PER_CLK_SM * GB300_SMS * GB300_SM_GHZ * 1e9
+    return rate / fp64_inst_per_flup(force, trt) / 1e6
+
+
+def bound_roof(variant: str, indirect: bool, precision: str, hbm_gbs: float, force: bool = False,
+               trt: bool = False):
+    """(bound, roof MFLUP/s): the lower of the HBM and, for FP64, FP64-pipe roofs."""
+    hbm = roof_mflups(variant, indirect, precision, hbm_gbs)
+    if precision == "f64":
+        alu = fp64_roof_mflups(force, trt)
+        if alu < hbm:
+            return "alu", alu
+    return "hbm", hbm
+
+
 def kernel_bytes_per_flup(variant: str, indirect: bool, precision: str, odd: bool = False) -> float:
     """Algorithmic DRAM bytes per FLUP of ONE launch of the variant's main
     kernel (the AA pattern's even and odd kernels differ)."""
