@@ -33,6 +33,9 @@ struct SwapPass {
   int start[3], count[3];      // tiles of this colour per axis: start + 2k (or the odd tail tile)
 };
 
+// full tile box (cells): 32 along x (one warp per row), 4 along y, 2 along z
+constexpr int kSwapTX = 32, kSwapTY = 4, kSwapTZ = 2;
+
 __device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
   if (nt == 1) return 0;
   if (periodic && (nt & 1)) return t == nt - 1 ? 2 : (t & 1);
@@ -87,18 +90,21 @@ __device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp,
 // it in shared memory, same layout; it may alias S).  Phase 2: each node
 // gathers the PDFs that end in its slots and writes them, and completes its
 // links to tiles of earlier colours in global memory.
-template <class C, int AOS, bool FORCE>
+// FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
+// size), so shared-memory offsets are compile-time constants.
+template <class C, int AOS, bool FORCE, bool FIXED>
 __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
                                           const typename C::S *stage, const int org[3], unsigned em, unsigned sm,
                                           double &m, double &jsum) {
   using T = typename C::T;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const Grid &g = p.g;
-  const int TN = sp.tx * sp.ty * sp.tz;
-  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int TX = FIXED ? kSwapTX : sp.tx, TY = FIXED ? kSwapTY : sp.ty, TZ = FIXED ? kSwapTZ : sp.tz;
+  const int TN = TX * TY * TZ;
   const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
+  const int t = lx + TX * (ly + TY * lz);
   // extent of this tile inside the box (the last tile of an axis may be cut)
-  const int ex = min(sp.tx, g.nx - org[0]), ey = min(sp.ty, g.ny - org[1]), ez = min(sp.tz, g.nz - org[2]);
+  const int ex = min(TX, g.nx - org[0]), ey = min(TY, g.ny - org[1]), ez = min(TZ, g.nz - org[2]);
   DirectNode nd;
   bool active = lx < ex && ly < ey && lz < ez;
   if (active) {
@@ -150,7 +156,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         }
       }
       if (in_x && in_y && in_z) {
-        v[i] = S[i * TN + t + dx + sp.tx * (dy + sp.ty * dz)];  // inside the tile
+        v[i] = S[i * TN + t + dx + TX * (dy + TY * dz)];  // inside the tile
         continue;
       }
       const int bit = tile_bit(in_x ? 0 : dx, in_y ? 0 : dy, in_z ? 0 : dz);
@@ -159,7 +165,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         const int wx = in_x ? lx + dx : (dx < 0 ? ex - 1 : 0);
         const int wy = in_y ? ly + dy : (dy < 0 ? ey - 1 : 0);
         const int wz = in_z ? lz + dz : (dz < 0 ? ez - 1 : 0);
-        v[i] = S[i * TN + wx + sp.tx * (wy + sp.ty * wz)];
+        v[i] = S[i * TN + wx + TX * (wy + TY * wz)];
       } else if (em & (1u << bit)) {
         // earlier tile: its reversed slot holds the PDF for us; ours goes there
         if (nd.fast) src = nd.nb_fast(p, OPP(i));
@@ -179,7 +185,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
 }
 
 // One pass: the tiles of one colour, one block per tile.
-template <class C, int AOS, bool IND, bool FORCE, bool RED>
+template <class C, int AOS, bool FORCE, bool RED, bool FIXED>
 __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, SwapPass sp) {
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
   __syncthreads();
   double m = 0.0, jsum = 0.0;
-  swap_tile<C, AOS, FORCE>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
+  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
   if (RED) block_reduce_store(m, jsum, p.partials);
 }
 
@@ -257,7 +263,7 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
   g_wait_selftest = mbar_wait(&bar, 0, limit_ns) ? 1 : 2;
 }
 
-template <class C, bool FORCE, bool RED>
+template <class C, bool FORCE, bool RED, bool FIXED>
 __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
   using T = typename C::T;
   using S = typename C::S;
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
     T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
     const unsigned em = masks[b][0], sm = masks[b][1];
-    swap_tile<C, 0, FORCE>(p, sp, Sbuf, stage[b], org, em, sm, m, jsum);
+    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], org, em, sm, m, jsum);
     // every thread read this buffer's bits before the barrier inside swap_tile
     if (t == 0) masks[b][0] = masks[b][1] = 0u;
     __syncthreads();
@@ -336,7 +342,8 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchSwap {
   static void run(const StepParams &p, const SwapPass &sp, size_t smem, dim3 blocks, cudaStream_t s) {
-    auto k = k_swap_pass<C, AOS, false, FORCE, RED>;
+    const bool fixed = sp.tx == kSwapTX && sp.ty == kSwapTY && sp.tz == kSwapTZ;
+    auto k = fixed ? k_swap_pass<C, AOS, FORCE, RED, true> : k_swap_pass<C, AOS, FORCE, RED, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp);
   }
@@ -351,7 +358,8 @@ struct LaunchSwapTma {
                   cudaStream_t s, int *launched) {
     *launched = 0;
     if constexpr (AOS == 0 && !IND) {
-      auto k = k_swap_tma<C, FORCE, RED>;
+      const bool fixed = sp.tx == kSwapTX && sp.ty == kSwapTY && sp.tz == kSwapTZ;
+      auto k = fixed ? k_swap_tma<C, FORCE, RED, true> : k_swap_tma<C, FORCE, RED, false>;
       const int threads = sp.tx * sp.ty * sp.tz;
       const size_t smem = swap_tma_smem_bytes(threads, sizeof(typename C::S), sizeof(typename C::T));
       if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
