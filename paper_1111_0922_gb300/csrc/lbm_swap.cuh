@@ -1,0 +1,452 @@
+// Swap algorithm (Sec. 5, Fig. 3, Tab. 4) on a full grid, push form, blocked.
+//
+// The serial swap collides a node into its reversed slots (the post-collision
+// PDF along c_i goes to the node's slot of the opposite direction) and then
+// completes each link to an already visited neighbour by exchanging the two
+// PDFs that travel along it; a link into a wall or solid needs no exchange.
+// That gives the natural next state for any visiting order in which a link is
+// exchanged after both of its nodes have collided.
+//
+// Here the order is blocked, as Sec. 5 allows: the box is cut into tiles, one
+// CTA per tile, and the tiles are coloured so that no two tiles sharing a link
+// have the same colour (per axis: tile index mod 2, a third colour for the
+// last tile of an odd periodic axis).  Colours run as consecutive launches.
+// Inside a CTA every node collides into shared memory; links inside the tile
+// are completed there; a link to a tile of an earlier colour is completed by
+// exchanging with global memory (that tile left its end reversed); a link to a
+// tile of a later colour is left reversed for that tile to complete.
+//
+// Kernels and launch templates; lbm_swap_f64.cu / _f32.cu / _f16s.cu
+// instantiate them per storage precision, lbm_swap.cu holds the host side.
+#pragma once
+
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "lbm_dispatch.cuh"
+#include "lbm_internal.h"
+
+namespace lbmk {
+
+struct SwapPass {
+  int tx, ty, tz;              // tile extent
+  int ntx, nty, ntz;           // tiles per axis
+  int cx, cy, cz;              // colours per axis
+  int colour;                  // colour of this pass (cx-fastest)
+  int start[3], count[3];      // tiles of this colour per axis: start + 2k (or the odd tail tile)
+};
+
+// full tile box (cells): 32 along x (one warp per row), 4 along y, 2 along z
+constexpr int kSwapTX = 32, kSwapTY = 4, kSwapTZ = 2;
+
+__device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
+  if (nt == 1) return 0;
+  if (periodic && (nt & 1)) return t == nt - 1 ? 2 : (t & 1);
+  return t & 1;
+}
+
+// Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
+__host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
+
+// Classify one of the 27 tile offsets l (o = (l%3 - 1, (l/3)%3 - 1, l/9 - 1),
+// so l = tile_bit(o)) of `tile` for this pass: `earlier` when that neighbour
+// exists and has an earlier colour, `self` when the tile is its own neighbour
+// across a periodic face.  The threads of a block take the offsets in
+// parallel and OR the bits together in shared memory.
+__device__ __forceinline__ void classify_offset(const Grid &g, const SwapPass &sp, const int tile[3], int l,
+                                                bool &earlier, bool &self) {
+  const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, l / 9 - 1};
+  const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
+  const int per[3] = {g.px, g.py, g.pz};
+  bool exists = true;
+  self = true;
+  int nb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nb[a] = tile[a] + o[a];
+    if (nb[a] < 0 || nb[a] >= nt[a]) {
+      if (!per[a]) exists = false;
+      nb[a] = (nb[a] + nt[a]) % nt[a];
+    }
+    self = self && nb[a] == tile[a];
+  }
+  const int col = axis_colour(nb[0], nt[0], per[0]) +
+                  sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
+  earlier = exists && !self && col < sp.colour;
+  self = exists && self;
+}
+
+__device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp, const int tile[3], int t, int nthreads,
+                                              unsigned *em, unsigned *sm) {
+  for (int l = t; l < 27; l += nthreads) {
+    bool e, f;
+    classify_offset(g, sp, tile, l, e, f);
+    if (e) atomicOr(em, 1u << l);
+    if (f) atomicOr(sm, 1u << l);
+  }
+}
+
+// One tile, all threads of the block (thread (lx, ly, lz) owns cell
+// org + (lx, ly, lz)).  Phase 1: every node collides; its post-collision
+// PDFs go to S[i * TN + t] (S in shared memory).  The node's stored PDFs
+// come from global memory, or from `stage` (the tile as the tensor copy left
+// it in shared memory, same layout; it may alias S).  Phase 2: each node
+// gathers the PDFs that end in its slots and writes them, and completes its
+// links to tiles of earlier colours in global memory.
+// FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
+// size), so shared-memory offsets are compile-time constants.
+template <class C, int AOS, bool FORCE, bool FIXED>
+__device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
+                                          const typename C::S *stage, const int org[3], unsigned em, unsigned sm,
+                                          double &m, double &jsum) {
+  using T = typename C::T;
+  Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
+  const Grid &g = p.g;
+  const int TX = FIXED ? kSwapTX : sp.tx, TY = FIXED ? kSwapTY : sp.ty, TZ = FIXED ? kSwapTZ : sp.tz;
+  const int TN = TX * TY * TZ;
+  const int lx = threadIdx.x, ly = threadIdx.y, lz = threadIdx.z;
+  const int t = lx + TX * (ly + TY * lz);
+  // extent of this tile inside the box (the last tile of an axis may be cut)
+  const int ex = min(TX, g.nx - org[0]), ey = min(TY, g.ny - org[1]), ez = min(TZ, g.nz - org[2]);
+  DirectNode nd;
+  bool active = lx < ex && ly < ey && lz < ez;
+  if (active) {
+    nd.x = org[0] + lx;
+    nd.y = org[1] + ly;
+    nd.z = org[2] + lz;
+    active = nd.setup(g);
+  }
+  if (active) {
+    T d[Q];
+    if (stage) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = C::raw(stage[i * TN + t]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
+    }
+    T drho, rjx;
+    collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
+    m += 1.0 + (double)drho;
+    jsum += (double)rjx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) S[i * TN + t] = d[i];
+  }
+  __syncthreads();
+  // Full tile whose nodes all have every neighbour (no solid mask, no wall
+  // face touching the tile): the branch structure below is uniform over each
+  // warp (one warp = one row of 32 cells), the x faces are fixed up after.
+  bool tile_fast = FIXED && g.solid == nullptr && ex == TX && ey == TY && ez == TZ;
+  if (FIXED) {
+    tile_fast = tile_fast && (g.px || (org[0] > 0 && org[0] + TX < g.nx)) &&
+                (g.py || (org[1] > 0 && org[1] + TY < g.ny)) && (g.pz || (org[2] > 0 && org[2] + TZ < g.nz));
+  }
+  if (FIXED && tile_fast && active) {
+    T v[Q];
+    int remote[Q];
+    unsigned xfix = 0;  // x-crossing directions this lane completes after the loop
+    v[0] = S[t];
+    const bool xm = lx == 0, xp = lx == TX - 1, ym = ly == 0, yp = ly == TY - 1, zm = lz == 0, zp = lz == TZ - 1;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      remote[i] = -1;
+      // the PDF arriving along c_i comes from x - c_i: outside the tile on
+      // axis a when c_a > 0 at the low face or c_a < 0 at the high face
+      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      const bool ox = cx > 0 ? xm : (cx < 0 ? xp : false);
+      const bool oy = cy > 0 ? ym : (cy < 0 ? yp : false);
+      const bool oz = cz > 0 ? zm : (cz < 0 ? zp : false);
+      const int inside = i * TN + t - (cx + TX * (cy + TY * cz));
+      if (!(oy || oz)) {  // uniform over the warp
+        if (cx == 0) {
+          v[i] = S[inside];
+        } else {
+          v[i] = S[ox ? OPP(i) * TN + t : inside];  // the x face is completed below
+          if (ox) xfix |= 1u << i;
+        }
+        continue;
+      }
+      const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
+      if (sm & (1u << bit)) {
+        const int wx = ox ? (cx > 0 ? TX - 1 : 0) : lx - cx;
+        const int wy = oy ? (cy > 0 ? TY - 1 : 0) : ly - cy;
+        const int wz = oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz;
+        v[i] = S[i * TN + wx + TX * (wy + TY * wz)];
+      } else if (em & (1u << bit)) {
+        const int src = nd.nb_fast(p, OPP(i));
+        remote[i] = src;
+        v[i] = L.ld(OPP(i), src);
+      } else {
+        v[i] = S[OPP(i) * TN + t];
+      }
+    }
+    if (xfix) {  // lanes 0 and 31 only
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = CX(i);
+        if (cx == 0 || !(xfix & (1u << i))) continue;
+        const int bit = tile_bit(-cx, 0, 0);
+        if (sm & (1u << bit)) {
+          v[i] = S[i * TN + (cx > 0 ? TX - 1 : 0) + TX * ((ly - CY(i)) + TY * (lz - CZ(i)))];
+        } else if (em & (1u << bit)) {
+          const int src = nd.nb_fast(p, OPP(i));
+          remote[i] = src;
+          v[i] = L.ld(OPP(i), src);
+        }
+      }
+    }
+    nd.launder_all();
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      L.st(i, nd.s, v[i]);
+      if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
+    }
+  } else if (active) {
+    // Gather every incoming value first (the loads from earlier tiles are
+    // independent and overlap), then write: the remote slots written below
+    // belong to earlier tiles and are never read by this pass again.
+    T v[Q];
+    int remote[Q];
+    v[0] = S[t];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      remote[i] = -1;
+      // the PDF arriving along c_i comes from x - c_i
+      const int dx = -CX(i), dy = -CY(i), dz = -CZ(i);
+      const bool in_x = dx == 0 || (dx < 0 ? lx > 0 : lx < ex - 1);
+      const bool in_y = dy == 0 || (dy < 0 ? ly > 0 : ly < ey - 1);
+      const bool in_z = dz == 0 || (dz < 0 ? lz > 0 : lz < ez - 1);
+      // source slot, or -1 across a wall or from a solid cell (a fast node
+      // has neither, and needs the slot only for a remote exchange)
+      int src = 0;
+      if (!nd.fast) {
+        src = nd.nb(p, OPP(i));
+        if (src < 0) {
+          v[i] = S[OPP(i) * TN + t];  // bounce-back: the node's own reversed PDF
+          continue;
+        }
+      }
+      if (in_x && in_y && in_z) {
+        v[i] = S[i * TN + t + dx + TX * (dy + TY * dz)];  // inside the tile
+        continue;
+      }
+      const int bit = tile_bit(in_x ? 0 : dx, in_y ? 0 : dy, in_z ? 0 : dz);
+      if (sm & (1u << bit)) {
+        // the tile is its own neighbour across a periodic face
+        const int wx = in_x ? lx + dx : (dx < 0 ? ex - 1 : 0);
+        const int wy = in_y ? ly + dy : (dy < 0 ? ey - 1 : 0);
+        const int wz = in_z ? lz + dz : (dz < 0 ? ez - 1 : 0);
+        v[i] = S[i * TN + wx + TX * (wy + TY * wz)];
+      } else if (em & (1u << bit)) {
+        // earlier tile: its reversed slot holds the PDF for us; ours goes there
+        if (nd.fast) src = nd.nb_fast(p, OPP(i));
+        remote[i] = src;
+        v[i] = L.ld(OPP(i), src);
+      } else {
+        v[i] = S[OPP(i) * TN + t];  // a later tile completes the link
+      }
+    }
+    nd.launder_all();
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      L.st(i, nd.s, v[i]);
+      if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
+    }
+  }
+}
+
+// One pass: the tiles of one colour, one block per tile.
+template <class C, int AOS, bool FORCE, bool RED, bool FIXED>
+__global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, SwapPass sp) {
+  using T = typename C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *S = reinterpret_cast<T *>(smem_raw);
+  __shared__ unsigned earlier_mask, self_mask;
+  const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
+                       sp.start[2] + 2 * (int)blockIdx.z};
+  const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (t == 0) earlier_mask = self_mask = 0u;
+  __syncthreads();
+  classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
+  __syncthreads();
+  double m = 0.0, jsum = 0.0;
+  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
+  if (RED) block_reduce_store(m, jsum, p.partials);
+}
+
+// ---------------------------------------------------------------------------
+// The same pass with the tiles staged by the tensor memory accelerator: a
+// persistent block walks its share of the pass's tiles and, while it works
+// on one tile, the tensor copy of its next tile (all 19 arrays of the tile's
+// box in one 4D copy: x, y, z, array) is already in flight into the other of
+// two shared-memory buffers.  Every wait on a copy is bounded by a time
+// limit; on expiry the block records the timeout and stops.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// true when the phase with the given parity has completed before limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t a = smem_addr(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr uint64_t kTmaWaitNs = 1000000000ull;  // 1 s
+
+template <class C, bool FORCE, bool RED, bool FIXED>
+__global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
+  using T = typename C::T;
+  using S = typename C::S;
+  constexpr bool kInPlace = sizeof(T) == sizeof(S);  // F32, F64: collide into the staged buffer
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ unsigned masks[2][2];  // [buffer][earlier, self]
+  const int TN = sp.tx * sp.ty * sp.tz;
+  const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
+  const size_t stage_pad = (stage_bytes + 127) / 128 * 128;
+  // tensor-copy destinations on 128-byte boundaries (the launch adds 128
+  // bytes of slack for this)
+  unsigned char *base = smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u);
+  S *stage[2] = {reinterpret_cast<S *>(base), reinterpret_cast<S *>(base + stage_pad)};
+  T *Sx = reinterpret_cast<T *>(base + 2 * stage_pad);  // separate buffer when not in place
+  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int ntiles = sp.count[0] * sp.count[1] * sp.count[2];
+  auto tile_of = [&](int n, int tile[3]) {
+    tile[0] = sp.start[0] + 2 * (n % sp.count[0]);
+    tile[1] = sp.start[1] + 2 * ((n / sp.count[0]) % sp.count[1]);
+    tile[2] = sp.start[2] + 2 * (n / (sp.count[0] * sp.count[1]));
+  };
+  auto issue = [&](int n, int b) {
+    int tile[3];
+    tile_of(n, tile);
+    mbar_expect_tx(&bar[b], (uint32_t)stage_bytes);
+    tma_load_4d(stage[b], &map, tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz, 0, &bar[b]);
+  };
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    masks[0][0] = masks[0][1] = masks[1][0] = masks[1][1] = 0u;
+  }
+  __syncthreads();
+  double m = 0.0, jsum = 0.0;
+  const int G = gridDim.x;
+  if (t == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int it = 0;
+  for (int n = blockIdx.x; n < ntiles; n += G, ++it) {
+    const int b = it & 1;
+    int tile[3];
+    tile_of(n, tile);
+    if (t == 0) {
+      // the other buffer was last read in the previous iteration, which
+      // ended with a block barrier; order those generic-proxy accesses
+      // before the tensor copy overwrites it
+      if (n + G < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(n + G, b ^ 1);
+      }
+    }
+    // (the bits of this buffer were cleared when it was last used)
+    classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &masks[b][0], &masks[b][1]);
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(p.err + 1, 1);
+        // let the copies still in flight land before the block exits
+        mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
+        if (n + G < ntiles) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitNs);
+      }
+      break;
+    }
+    const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
+    T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
+    const unsigned em = masks[b][0], sm = masks[b][1];
+    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], org, em, sm, m, jsum);
+    // every thread read this buffer's bits before the barrier inside swap_tile
+    if (t == 0) masks[b][0] = masks[b][1] = 0u;
+    __syncthreads();
+  }
+  if (RED) block_reduce_store(m, jsum, p.partials);
+}
+
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+struct LaunchSwap {
+  static void run(const StepParams &p, const SwapPass &sp, size_t smem, dim3 blocks, cudaStream_t s) {
+    const bool fixed = sp.tx == kSwapTX && sp.ty == kSwapTY && sp.tz == kSwapTZ;
+    auto k = fixed ? k_swap_pass<C, AOS, FORCE, RED, true> : k_swap_pass<C, AOS, FORCE, RED, false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp);
+  }
+};
+
+// Persistent launch: as many blocks as fit on the GPU at once (resident
+// blocks per SM for this block shape and shared memory x SMs), at most one
+// per tile.  Returns the number of blocks launched.
+template <class C, int AOS, bool IND, bool FORCE, bool RED>
+struct LaunchSwapTma {
+  static void run(const StepParams &p, const SwapPass &sp, const CUtensorMap *map, int nsm, int ntiles,
+                  cudaStream_t s, int *launched) {
+    *launched = 0;
+    if constexpr (AOS == 0 && !IND) {
+      const bool fixed = sp.tx == kSwapTX && sp.ty == kSwapTY && sp.tz == kSwapTZ;
+      auto k = fixed ? k_swap_tma<C, FORCE, RED, true> : k_swap_tma<C, FORCE, RED, false>;
+      const int threads = sp.tx * sp.ty * sp.tz;
+      const size_t smem = swap_tma_smem_bytes(threads, sizeof(typename C::S), sizeof(typename C::T));
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+      const int grid = std::min(ntiles, per_sm * std::max(nsm, 1));
+      k<<<grid, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp, *map);
+      *launched = grid;
+    }
+  }
+};
+
+// Per-precision entry points (instantiated in lbm_swap_<precision>.cu).
+template <class C>
+void swap_pass_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, size_t smem, cudaStream_t s) {
+  const dim3 blocks(sp.count[0], sp.count[1], sp.count[2]);
+  dispatch_layout<LaunchSwap, C>(k.aos, false, k.force, k.red, p, sp, smem, blocks, s);
+}
+template <class C>
+int swap_pass_tma_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, const CUtensorMap *map, int nsm,
+                    int ntiles, cudaStream_t s) {
+  int launched = 0;
+  dispatch_layout<LaunchSwapTma, C>(0, false, k.force, k.red, p, sp, map, nsm, ntiles, s, &launched);
+  return launched;
+}
+
+}  // namespace lbmk
