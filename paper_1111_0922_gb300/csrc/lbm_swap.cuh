@@ -181,15 +181,19 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         v[i] = S[OPP(i) * TN + t];
       }
     }
-    if (xfix) {  // lanes 0 and 31 only
+    // x faces: lane 0 completes its links to the tile on the left, lane 31
+    // those to the tile on the right (one class per side, uniform per tile)
+    const int side = xm ? -1 : (xp ? 1 : 0);  // offset of the x neighbour tile
+    const int sbit = tile_bit(side, 0, 0);
+    if (side != 0 && xfix && ((sm | em) & (1u << sbit))) {
+      const bool self_x = (sm & (1u << sbit)) != 0;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const int cx = CX(i);
         if (cx == 0 || !(xfix & (1u << i))) continue;
-        const int bit = tile_bit(-cx, 0, 0);
-        if (sm & (1u << bit)) {
+        if (self_x) {
           v[i] = S[i * TN + (cx > 0 ? TX - 1 : 0) + TX * ((ly - CY(i)) + TY * (lz - CZ(i)))];
-        } else if (em & (1u << bit)) {
+        } else {
           const int src = nd.nb_fast(p, OPP(i));
           remote[i] = src;
           v[i] = L.ld(OPP(i), src);
@@ -297,18 +301,21 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-// true when the phase with the given parity has completed before limit_ns
+// true when the phase with the given parity has completed before limit_ns.
+// Each try_wait suspends the thread until the phase completes or about 20 us
+// pass, so a waiting warp takes almost no issue slots.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = smem_addr(bar);
+  const uint32_t hint_ns = 20000;
   const uint64_t t0 = global_ns();
   while (true) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred P;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, P;\n\t}"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(hint_ns)
         : "memory");
     if (ok) return true;
     if (global_ns() - t0 > limit_ns) return false;
