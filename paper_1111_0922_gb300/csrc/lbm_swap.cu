@@ -31,8 +31,12 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
 }
 
 // tiles are at most 32 x 4 x 2 = 256 cells (one thread each)
+// S (19 post-collision PDFs per cell, compute type) and the remote-prefetch
+// buffer (18 words per cell, the stored element or its 4-byte word)
 size_t swap_smem_bytes(const SwapTiles &t, int precision) {
-  return (size_t)Q * t.tx * t.ty * t.tz * (precision == 0 ? 8 : 4);
+  const size_t cells = (size_t)t.tx * t.ty * t.tz;
+  const size_t comp = precision == 0 ? 8 : 4, word = precision == 0 ? 8 : 4;
+  return ((size_t)Q * cells * comp + 15) / 16 * 16 + (size_t)(Q - 1) * cells * word;
 }
 
 static void axis_set(int nt, int periodic, int colour, int &start, int &count) {
@@ -99,7 +103,9 @@ int launch_swap_pass_tma(const StepParams &p, const SwapTiles &t, const KernelKe
 
 size_t swap_tma_smem_bytes(int tile_cells, size_t stored, size_t computed) {
   const size_t stage = ((size_t)Q * tile_cells * stored + 127) / 128 * 128;
-  return 128 + 2 * stage + (stored == computed ? 0 : (size_t)Q * tile_cells * computed);
+  const size_t sx = stored == computed ? 0 : ((size_t)Q * tile_cells * computed + 15) / 16 * 16;
+  const size_t word = stored < 4 ? 4 : stored;
+  return 128 + 2 * stage + sx + (size_t)(Q - 1) * tile_cells * word;
 }
 
 int swap_colours(const SwapTiles &t, int px, int py, int pz) {

@@ -96,10 +96,81 @@ __device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp,
 // links to tiles of earlier colours in global memory.
 // FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
 // size), so shared-memory offsets are compile-time constants.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// true when the phase with the given parity has completed before limit_ns.
+// Each try_wait suspends the thread until the phase completes or about 20 us
+// pass, so a waiting warp takes almost no issue slots.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t a = smem_addr(bar);
+  const uint32_t hint_ns = 20000;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Word of the remote-prefetch buffer: the stored element, or for 2-byte
+// elements the aligned 4-byte word that holds it (asynchronous copies move 4,
+// 8 or 16 bytes).
+template <class C>
+using RemoteWord = typename std::conditional<sizeof(typename C::S) == 2, uint32_t, typename C::S>::type;
+
+template <class C>
+__device__ __forceinline__ void prefetch_remote(RemoteWord<C> *dst, const typename C::S *src) {
+  if constexpr (sizeof(typename C::S) == 2) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(a) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "n"(sizeof(typename C::S))
+                 : "memory");
+  }
+}
+// the prefetched element (odd slots are the high half of a 2-byte pair)
+template <class C>
+__device__ __forceinline__ typename C::T fetch_remote(const RemoteWord<C> &w, int slot) {
+  if constexpr (sizeof(typename C::S) == 2) {
+    const unsigned short h = (unsigned short)((slot & 1) ? (w >> 16) : (w & 0xffffu));
+    return C::raw(__ushort_as_half(h));
+  } else {
+    return C::raw(w);
+  }
+}
+
 template <class C, int AOS, bool FORCE, bool FIXED>
 __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
-                                          const typename C::S *stage, const int org[3], unsigned em, unsigned sm,
-                                          double &m, double &jsum) {
+                                          const typename C::S *stage, RemoteWord<C> *R, const int org[3],
+                                          unsigned em, unsigned sm, double &m, double &jsum) {
   using T = typename C::T;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const Grid &g = p.g;
@@ -116,6 +187,33 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
     nd.y = org[1] + ly;
     nd.z = org[2] + lz;
     active = nd.setup(g);
+  }
+  // Full tile whose nodes all have every neighbour (no solid mask, no wall
+  // face touching the tile): the branch structure below is uniform over each
+  // warp (one warp = one row of 32 cells), the x faces are fixed up after.
+  bool tile_fast = FIXED && g.solid == nullptr && ex == TX && ey == TY && ez == TZ;
+  if (FIXED) {
+    tile_fast = tile_fast && (g.px || (org[0] > 0 && org[0] + TX < g.nx)) &&
+                (g.py || (org[1] > 0 && org[1] + TY < g.ny)) && (g.pz || (org[2] > 0 && org[2] + TZ < g.nz));
+  }
+  const bool xm = lx == 0, xp = lx == TX - 1, ym = ly == 0, yp = ly == TY - 1, zm = lz == 0, zp = lz == TZ - 1;
+  // Links to tiles of earlier colours: start the copies of their reversed
+  // slots now, so that the collision below covers the memory latency.
+  unsigned rmask = 0;
+  if (FIXED && tile_fast && active) {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = CX(i), cy = CY(i), cz = CZ(i);
+      const bool ox = cx > 0 ? xm : (cx < 0 ? xp : false);
+      const bool oy = cy > 0 ? ym : (cy < 0 ? yp : false);
+      const bool oz = cz > 0 ? zm : (cz < 0 ? zp : false);
+      if (!(ox || oy || oz)) continue;
+      const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
+      if (!(em & (1u << bit))) continue;
+      prefetch_remote<C>(&R[(i - 1) * TN + t], L.at(OPP(i), nd.nb_fast(p, OPP(i))));
+      rmask |= 1u << i;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
   if (active) {
     T d[Q];
@@ -134,20 +232,12 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
     for (int i = 0; i < Q; ++i) S[i * TN + t] = d[i];
   }
   __syncthreads();
-  // Full tile whose nodes all have every neighbour (no solid mask, no wall
-  // face touching the tile): the branch structure below is uniform over each
-  // warp (one warp = one row of 32 cells), the x faces are fixed up after.
-  bool tile_fast = FIXED && g.solid == nullptr && ex == TX && ey == TY && ez == TZ;
-  if (FIXED) {
-    tile_fast = tile_fast && (g.px || (org[0] > 0 && org[0] + TX < g.nx)) &&
-                (g.py || (org[1] > 0 && org[1] + TY < g.ny)) && (g.pz || (org[2] > 0 && org[2] + TZ < g.nz));
-  }
   if (FIXED && tile_fast && active) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's prefetches
     T v[Q];
     int remote[Q];
     unsigned xfix = 0;  // x-crossing directions this lane completes after the loop
     v[0] = S[t];
-    const bool xm = lx == 0, xp = lx == TX - 1, ym = ly == 0, yp = ly == TY - 1, zm = lz == 0, zp = lz == TZ - 1;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       remote[i] = -1;
@@ -173,10 +263,10 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         const int wy = oy ? (cy > 0 ? TY - 1 : 0) : ly - cy;
         const int wz = oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz;
         v[i] = S[i * TN + wx + TX * (wy + TY * wz)];
-      } else if (em & (1u << bit)) {
+      } else if (rmask & (1u << i)) {
         const int src = nd.nb_fast(p, OPP(i));
         remote[i] = src;
-        v[i] = L.ld(OPP(i), src);
+        v[i] = fetch_remote<C>(R[(i - 1) * TN + t], src);
       } else {
         v[i] = S[OPP(i) * TN + t];
       }
@@ -196,7 +286,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         } else {
           const int src = nd.nb_fast(p, OPP(i));
           remote[i] = src;
-          v[i] = L.ld(OPP(i), src);
+          v[i] = fetch_remote<C>(R[(i - 1) * TN + t], src);
         }
       }
     }
@@ -266,6 +356,8 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);
+  const int TN = sp.tx * sp.ty * sp.tz;
+  RemoteWord<C> *R = reinterpret_cast<RemoteWord<C> *>(smem_raw + ((size_t)Q * TN * sizeof(T) + 15) / 16 * 16);
   __shared__ unsigned earlier_mask, self_mask;
   const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
                        sp.start[2] + 2 * (int)blockIdx.z};
@@ -276,7 +368,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
   __syncthreads();
   double m = 0.0, jsum = 0.0;
-  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, org, earlier_mask, self_mask, m, jsum);
+  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, R, org, earlier_mask, self_mask, m, jsum);
   if (RED) block_reduce_store(m, jsum, p.partials);
 }
 
@@ -287,49 +379,6 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
 // box in one 4D copy: x, y, z, array) is already in flight into the other of
 // two shared-memory buffers.  Every wait on a copy is bounded by a time
 // limit; on expiry the block records the timeout and stops.
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// true when the phase with the given parity has completed before limit_ns.
-// Each try_wait suspends the thread until the phase completes or about 20 us
-// pass, so a waiting warp takes almost no issue slots.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-  const uint32_t a = smem_addr(bar);
-  const uint32_t hint_ns = 20000;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, P;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity), "r"(hint_ns)
-        : "memory");
-    if (ok) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-}
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-      : "memory");
-}
-
 constexpr uint64_t kTmaWaitNs = 1000000000ull;  // 1 s
 
 template <class C, bool FORCE, bool RED, bool FIXED>
@@ -348,6 +397,8 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   unsigned char *base = smem_tma + ((128u - (smem_addr(smem_tma) & 127u)) & 127u);
   S *stage[2] = {reinterpret_cast<S *>(base), reinterpret_cast<S *>(base + stage_pad)};
   T *Sx = reinterpret_cast<T *>(base + 2 * stage_pad);  // separate buffer when not in place
+  const size_t sx_bytes = kInPlace ? 0 : ((size_t)Q * TN * sizeof(T) + 15) / 16 * 16;
+  RemoteWord<C> *R = reinterpret_cast<RemoteWord<C> *>(base + 2 * stage_pad + sx_bytes);
   const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int ntiles = sp.count[0] * sp.count[1] * sp.count[2];
   auto tile_of = [&](int n, int tile[3]) {
@@ -400,7 +451,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
     T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
     const unsigned em = masks[b][0], sm = masks[b][1];
-    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], org, em, sm, m, jsum);
+    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], R, org, em, sm, m, jsum);
     // every thread read this buffer's bits before the barrier inside swap_tile
     if (t == 0) masks[b][0] = masks[b][1] = 0u;
     __syncthreads();
@@ -431,6 +482,7 @@ struct LaunchSwapTma {
       auto k = fixed ? k_swap_tma<C, FORCE, RED, true> : k_swap_tma<C, FORCE, RED, false>;
       const int threads = sp.tx * sp.ty * sp.tz;
       const size_t smem = swap_tma_smem_bytes(threads, sizeof(typename C::S), sizeof(typename C::T));
+      static_assert(sizeof(RemoteWord<C>) == (sizeof(typename C::S) < 4 ? 4 : sizeof(typename C::S)), "word");
       if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       int per_sm = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
