@@ -94,6 +94,35 @@ __device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp,
 // it in shared memory, same layout; it may alias S).  Phase 2: each node
 // gathers the PDFs that end in its slots and writes them, and completes its
 // links to tiles of earlier colours in global memory.
+// Link classes of a full 32 x 4 x 2 tile.  A cell's links depend only on
+// which faces it lies on: x low / inner / high, y low / inner / high, z low /
+// high, 18 cell classes c = xc + 3 (yc + 3 zc).  For each class and
+// direction i (bit i) the table holds: [0] the source x - c_i lies outside
+// the tile, [1] ... in a tile of an earlier colour (a remote exchange),
+// [2] ... in the tile itself across a periodic face.  Threads t < 18 fill it.
+__device__ __forceinline__ void build_class_table(unsigned em, unsigned sm, int t, unsigned *cls) {
+  if (t >= 18) return;
+  const int xc = t % 3, yc = (t / 3) % 3, zc = t / 9;
+  unsigned om = 0, rm = 0, smk = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    const bool ox = cx > 0 ? xc == 0 : (cx < 0 ? xc == 2 : false);
+    const bool oy = cy > 0 ? yc == 0 : (cy < 0 ? yc == 2 : false);
+    const bool oz = cz > 0 ? zc == 0 : (cz < 0 ? zc == 1 : false);
+    if (!(ox || oy || oz)) continue;
+    om |= 1u << i;
+    const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
+    if (sm & (1u << bit))
+      smk |= 1u << i;
+    else if (em & (1u << bit))
+      rm |= 1u << i;
+  }
+  cls[3 * t] = om;
+  cls[3 * t + 1] = rm;
+  cls[3 * t + 2] = smk;
+}
+
 // FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
 // size), so shared-memory offsets are compile-time constants.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -169,8 +198,8 @@ __device__ __forceinline__ typename C::T fetch_remote(const RemoteWord<C> &w, in
 
 template <class C, int AOS, bool FORCE, bool FIXED>
 __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
-                                          const typename C::S *stage, RemoteWord<C> *R, const int org[3],
-                                          unsigned em, unsigned sm, double &m, double &jsum) {
+                                          const typename C::S *stage, RemoteWord<C> *R, const unsigned *cls,
+                                          const int org[3], unsigned em, unsigned sm, double &m, double &jsum) {
   using T = typename C::T;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const Grid &g = p.g;
@@ -199,20 +228,15 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
   const bool xm = lx == 0, xp = lx == TX - 1, ym = ly == 0, yp = ly == TY - 1, zm = lz == 0, zp = lz == TZ - 1;
   // Links to tiles of earlier colours: start the copies of their reversed
   // slots now, so that the collision below covers the memory latency.
-  unsigned rmask = 0;
+  unsigned omask = 0, rmask = 0, smask = 0;
   if (FIXED && tile_fast && active) {
+    const int c = (xm ? 0 : (xp ? 2 : 1)) + 3 * ((ym ? 0 : (yp ? 2 : 1)) + 3 * (zm ? 0 : 1));
+    omask = cls[3 * c];
+    rmask = cls[3 * c + 1];
+    smask = cls[3 * c + 2];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int cx = CX(i), cy = CY(i), cz = CZ(i);
-      const bool ox = cx > 0 ? xm : (cx < 0 ? xp : false);
-      const bool oy = cy > 0 ? ym : (cy < 0 ? yp : false);
-      const bool oz = cz > 0 ? zm : (cz < 0 ? zp : false);
-      if (!(ox || oy || oz)) continue;
-      const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
-      if (!(em & (1u << bit))) continue;
-      prefetch_remote<C>(&R[(i - 1) * TN + t], L.at(OPP(i), nd.nb_fast(p, OPP(i))));
-      rmask |= 1u << i;
-    }
+    for (int i = 1; i < Q; ++i)
+      if (rmask & (1u << i)) prefetch_remote<C>(&R[(i - 1) * TN + t], L.at(OPP(i), nd.nb_fast(p, OPP(i))));
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   if (active) {
@@ -234,67 +258,30 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
   __syncthreads();
   if (FIXED && tile_fast && active) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's prefetches
+    // Each slot i takes g_i(x - c_i): from the tile (inside), from the other
+    // end of the tile (its own neighbour across a periodic face), the node's
+    // own reversed PDF (a later tile completes the link), or the prefetched
+    // reversed slot of an earlier tile (whose slot then takes our PDF).
     T v[Q];
-    int remote[Q];
-    unsigned xfix = 0;  // x-crossing directions this lane completes after the loop
     v[0] = S[t];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      remote[i] = -1;
-      // the PDF arriving along c_i comes from x - c_i: outside the tile on
-      // axis a when c_a > 0 at the low face or c_a < 0 at the high face
       const int cx = CX(i), cy = CY(i), cz = CZ(i);
       const bool ox = cx > 0 ? xm : (cx < 0 ? xp : false);
       const bool oy = cy > 0 ? ym : (cy < 0 ? yp : false);
       const bool oz = cz > 0 ? zm : (cz < 0 ? zp : false);
       const int inside = i * TN + t - (cx + TX * (cy + TY * cz));
-      if (!(oy || oz)) {  // uniform over the warp
-        if (cx == 0) {
-          v[i] = S[inside];
-        } else {
-          v[i] = S[ox ? OPP(i) * TN + t : inside];  // the x face is completed below
-          if (ox) xfix |= 1u << i;
-        }
-        continue;
-      }
-      const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
-      if (sm & (1u << bit)) {
-        const int wx = ox ? (cx > 0 ? TX - 1 : 0) : lx - cx;
-        const int wy = oy ? (cy > 0 ? TY - 1 : 0) : ly - cy;
-        const int wz = oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz;
-        v[i] = S[i * TN + wx + TX * (wy + TY * wz)];
-      } else if (rmask & (1u << i)) {
-        const int src = nd.nb_fast(p, OPP(i));
-        remote[i] = src;
-        v[i] = fetch_remote<C>(R[(i - 1) * TN + t], src);
-      } else {
-        v[i] = S[OPP(i) * TN + t];
-      }
-    }
-    // x faces: lane 0 completes its links to the tile on the left, lane 31
-    // those to the tile on the right (one class per side, uniform per tile)
-    const int side = xm ? -1 : (xp ? 1 : 0);  // offset of the x neighbour tile
-    const int sbit = tile_bit(side, 0, 0);
-    if (side != 0 && xfix && ((sm | em) & (1u << sbit))) {
-      const bool self_x = (sm & (1u << sbit)) != 0;
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int cx = CX(i);
-        if (cx == 0 || !(xfix & (1u << i))) continue;
-        if (self_x) {
-          v[i] = S[i * TN + (cx > 0 ? TX - 1 : 0) + TX * ((ly - CY(i)) + TY * (lz - CZ(i)))];
-        } else {
-          const int src = nd.nb_fast(p, OPP(i));
-          remote[i] = src;
-          v[i] = fetch_remote<C>(R[(i - 1) * TN + t], src);
-        }
-      }
+      const int wrapped = i * TN + (ox ? (cx > 0 ? TX - 1 : 0) : lx - cx) +
+                          TX * ((oy ? (cy > 0 ? TY - 1 : 0) : ly - cy) + TY * (oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz));
+      const unsigned b = 1u << i;
+      v[i] = S[!(omask & b) ? inside : ((smask & b) ? wrapped : OPP(i) * TN + t)];
+      if (rmask & b) v[i] = fetch_remote<C>(R[(i - 1) * TN + t], nd.nb_fast(p, OPP(i)));
     }
     nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       L.st(i, nd.s, v[i]);
-      if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
+      if (i > 0 && (rmask & (1u << i))) L.st(OPP(i), nd.nb_fast(p, OPP(i)), S[OPP(i) * TN + t]);
     }
   } else if (active) {
     // Gather every incoming value first (the loads from earlier tiles are
@@ -359,6 +346,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   const int TN = sp.tx * sp.ty * sp.tz;
   RemoteWord<C> *R = reinterpret_cast<RemoteWord<C> *>(smem_raw + ((size_t)Q * TN * sizeof(T) + 15) / 16 * 16);
   __shared__ unsigned earlier_mask, self_mask;
+  __shared__ unsigned cls[54];
   const int tile[3] = {sp.start[0] + 2 * (int)blockIdx.x, sp.start[1] + 2 * (int)blockIdx.y,
                        sp.start[2] + 2 * (int)blockIdx.z};
   const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
@@ -367,8 +355,12 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   __syncthreads();
   classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
   __syncthreads();
+  if (FIXED) {
+    build_class_table(earlier_mask, self_mask, t, cls);
+    __syncthreads();
+  }
   double m = 0.0, jsum = 0.0;
-  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, R, org, earlier_mask, self_mask, m, jsum);
+  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, R, cls, org, earlier_mask, self_mask, m, jsum);
   if (RED) block_reduce_store(m, jsum, p.partials);
 }
 
@@ -389,6 +381,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   extern __shared__ __align__(128) unsigned char smem_tma[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ unsigned masks[2][2];  // [buffer][earlier, self]
+  __shared__ unsigned cls[54];
   const int TN = sp.tx * sp.ty * sp.tz;
   const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
   const size_t stage_pad = (stage_bytes + 127) / 128 * 128;
@@ -438,6 +431,10 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     }
     // (the bits of this buffer were cleared when it was last used)
     classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &masks[b][0], &masks[b][1]);
+    if (FIXED) {
+      __syncthreads();
+      build_class_table(masks[b][0], masks[b][1], t, cls);  // published by the vote below
+    }
     const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
@@ -451,7 +448,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
     T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
     const unsigned em = masks[b][0], sm = masks[b][1];
-    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], R, org, em, sm, m, jsum);
+    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], R, cls, org, em, sm, m, jsum);
     // every thread read this buffer's bits before the barrier inside swap_tile
     if (t == 0) masks[b][0] = masks[b][1] = 0u;
     __syncthreads();
