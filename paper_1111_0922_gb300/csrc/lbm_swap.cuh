@@ -270,11 +270,12 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
       const bool ox = cx > 0 ? xm : (cx < 0 ? xp : false);
       const bool oy = cy > 0 ? ym : (cy < 0 ? yp : false);
       const bool oz = cz > 0 ? zm : (cz < 0 ? zp : false);
-      const int inside = i * TN + t - (cx + TX * (cy + TY * cz));
-      const int wrapped = i * TN + (ox ? (cx > 0 ? TX - 1 : 0) : lx - cx) +
-                          TX * ((oy ? (cy > 0 ? TY - 1 : 0) : ly - cy) + TY * (oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz));
       const unsigned b = 1u << i;
-      v[i] = S[!(omask & b) ? inside : ((smask & b) ? wrapped : OPP(i) * TN + t)];
+      int a = !(omask & b) ? i * TN + t - (cx + TX * (cy + TY * cz)) : OPP(i) * TN + t;
+      if (smask & b)  // the tile's own far end (one tile along a periodic axis)
+        a = i * TN + (ox ? (cx > 0 ? TX - 1 : 0) : lx - cx) +
+            TX * ((oy ? (cy > 0 ? TY - 1 : 0) : ly - cy) + TY * (oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz));
+      v[i] = S[a];
       if (rmask & b) v[i] = fetch_remote<C>(R[(i - 1) * TN + t], nd.nb_fast(p, OPP(i)));
     }
     nd.launder_all();
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ unsigned masks[2][2];  // [buffer][earlier, self]
   __shared__ unsigned cls[54];
+  __shared__ int tiles[2][3];       // [buffer] tile coordinates, written with the copy's issue
   const int TN = sp.tx * sp.ty * sp.tz;
   const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
   const size_t stage_pad = (stage_bytes + 127) / 128 * 128;
@@ -402,6 +404,9 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   auto issue = [&](int n, int b) {
     int tile[3];
     tile_of(n, tile);
+    tiles[b][0] = tile[0];
+    tiles[b][1] = tile[1];
+    tiles[b][2] = tile[2];
     mbar_expect_tx(&bar[b], (uint32_t)stage_bytes);
     tma_load_4d(stage[b], &map, tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz, 0, &bar[b]);
   };
@@ -415,11 +420,11 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   double m = 0.0, jsum = 0.0;
   const int G = gridDim.x;
   if (t == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  __syncthreads();  // tiles[0]
   int it = 0;
   for (int n = blockIdx.x; n < ntiles; n += G, ++it) {
     const int b = it & 1;
-    int tile[3];
-    tile_of(n, tile);
+    const int tile[3] = {tiles[b][0], tiles[b][1], tiles[b][2]};
     if (t == 0) {
       // the other buffer was last read in the previous iteration, which
       // ended with a block barrier; order those generic-proxy accesses
