@@ -105,9 +105,10 @@ typedef struct lbm_config {
   int32_t store_hint;        /* LBM_OS_PUSH / LBM_OS_PULL, SoA: 1 = write the second lattice with
                                 cache-streaming (evict-first) stores, the GPU counterpart of the
                                 non-temporal stores of OS-NT (Sec. 3); 0 = ordinary stores */
-  int32_t tile_staging;      /* LBM_SWAP, full grid, SoA: 0 = stage each tile in shared memory with one
-                                tensor copy (TMA) when the row pitch is a multiple of 16 bytes,
-                                1 = plain loads */
+  int32_t tile_staging;      /* LBM_SWAP, full grid, SoA: 1 = stage each tile in shared memory with one
+                                tensor copy (TMA) in persistent blocks when the row pitch is a
+                                multiple of 16 bytes; 0 = one block per tile with plain loads
+                                (default: as fast or faster on GB300) */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

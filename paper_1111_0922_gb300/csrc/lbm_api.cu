@@ -560,7 +560,7 @@ static lbm_status build_geometry(lbm_t *h) {
     h->idx_folded = true;
   }
   h->swap_tma = false;
-  if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA && c.tile_staging == 0) {
+  if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA && c.tile_staging == 1) {
     // tensor copies need 16-byte row pitches and inner box extents
     const SwapTiles t = swap_tiles(h);
     const cuuint64_t es = (cuuint64_t)store_size(c.precision);

@@ -92,7 +92,7 @@ def main(argv=None):
     ap.add_argument("--store-hint", type=int, default=0,
                     help="OS push/pull, SoA: 1 = cache-streaming stores of the second lattice (OS-NT analogue)")
     ap.add_argument("--tile-staging", type=int, default=0,
-                    help="swap, full grid, SoA: 0 = tensor-copy tile staging when possible, 1 = plain loads")
+                    help="swap, full grid, SoA: 1 = tensor-copy tile staging when possible, 0 = plain loads")
     ap.add_argument("--trt", action="store_true", help="two-relaxation-time collision, magic 3/16")
     args = ap.parse_args(argv)
     import torch

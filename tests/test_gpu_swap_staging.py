@@ -46,8 +46,8 @@ def test_staged_swap_equals_plain_and_oracle(L, precision, dims, per):
     solid = (rng.random(n) < 0.1).astype(np.uint8)
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     g = (2e-5, 1e-5, -5e-6)
-    a, sa = _run(L, dims, per, precision, 0, solid, f0, 6, 1.2, g)
-    b, sb = _run(L, dims, per, precision, 1, solid, f0, 6, 1.2, g)
+    a, sa = _run(L, dims, per, precision, 1, solid, f0, 6, 1.2, g)
+    b, sb = _run(L, dims, per, precision, 0, solid, f0, 6, 1.2, g)
     assert sa == 1 and sb == 0
     assert np.array_equal(a, b)
     ref = oracle.run_push(dims, per, solid, f0, 6, 1.2, g)
@@ -62,7 +62,7 @@ def test_staged_swap_equals_plain_and_oracle(L, precision, dims, per):
 
 def test_rows_off_the_16_byte_grid_use_plain_loads(L):
     # FP32 rows of 70 cells are 280 bytes: no tensor copies
-    lat = L.Lattice((70, 8, 4), (1, 1, 1), variant="swap", precision="f32")
+    lat = L.Lattice((70, 8, 4), (1, 1, 1), variant="swap", precision="f32", tile_staging=1)
     lat.set_geometry(None)
     assert lat.info.tile_staged == 0
     lat.close()
