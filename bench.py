@@ -20,6 +20,7 @@ collective on the data path); value = total node updates / max rank time.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -71,17 +72,17 @@ def kernel_source_hash(names=HEADLINE_SOURCES):
 
 
 def profiled_traffic(kernel_key):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when the kernel sources changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
-    with open(p) as f:
-        d = json.load(f)
-    ent = d.get(kernel_key)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_launch_full")
+    """DRAM bytes per launch of a kernel from the committed ncu summary (a
+    line `dram_bytes_per_launch <key> <bytes> source_hash <hash>` in a file of
+    profiles/), or None when the kernel sources changed since the capture."""
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 5 and parts[0] == "dram_bytes_per_launch" and parts[1] == kernel_key \
+                        and parts[3] == "source_hash":
+                    return float(parts[2]) if parts[4] == kernel_source_hash() else None
+    return None
 
 
 # ---------------------------------------------------------------------------
