@@ -107,10 +107,17 @@ def fp64_roof_mflups(force: bool = False, trt: bool = False) -> float:
 
 def bound_roof(variant: str, indirect: bool, precision: str, hbm_gbs: float, force: bool = False,
                trt: bool = False):
-    """(bound, roof MFLUP/s): the lower of the HBM and, for FP64, FP64-pipe roofs."""
+    """(bound, roof MFLUP/s): the lower of the HBM and, for FP64, FP64-pipe
+    roofs.  The two-step scheme's FP64 roof adds the time of its stream
+    kernel (pure data movement, half of its bytes at HBM speed) to the
+    collide kernel's FP64-pipe time, since the two kernels run one after the
+    other."""
     hbm = roof_mflups(variant, indirect, precision, hbm_gbs)
     if precision == "f64":
         alu = fp64_roof_mflups(force, trt)
+        if variant == "ts":
+            stream_s = gpu_bytes(variant, indirect, precision) / 2 / (hbm_gbs * 1e9)
+            alu = 1.0 / (1.0 / (alu * 1e6) + stream_s) / 1e6
         if alu < hbm:
             return "alu", alu
     return "hbm", hbm
