@@ -71,7 +71,7 @@ typedef enum {
   LBM_ERR_BOUNDS = 5,       /* a kernel's bounds check tripped */
   LBM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
   LBM_ERR_NOT_CONVERGED = 7,/* a solve hit its step cap */
-  LBM_ERR_UNSUPPORTED = 8   /* valid request this build does not implement */
+  LBM_ERR_UNSUPPORTED = 8   /* valid request the library does not implement */
 } lbm_status;
 
 enum { LBM_TS = 0, LBM_OS_PUSH = 1, LBM_OS_PULL = 2, LBM_CG = 3, LBM_SWAP = 4, LBM_AA = 5, LBM_ET = 6 };
