@@ -212,7 +212,11 @@ static StepParams params_of(const lbm_t *h) {
   p.g = h->grid;
   p.idx = h->cfg.variant == LBM_ET ? h->d_etidx : h->d_idx;
   p.ipad = h->ipad;
-  for (int i = 0; i < Q; ++i) p.map[i] = h->map[i];
+  for (int i = 0; i < Q; ++i) {
+    p.map[i] = h->map[i];
+    p.mapbase[i] = h->d_A ? static_cast<char *>(p.A) + (int64_t)h->map[i] * h->npad * (int64_t)store_size(h->cfg.precision)
+                          : nullptr;
+  }
   p.omega = h->cfg.omega;
   p.omega_m = omega_minus(h->cfg);
   p.gx = h->cfg.force[0];

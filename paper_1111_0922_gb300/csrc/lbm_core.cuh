@@ -174,8 +174,9 @@ __device__ __forceinline__ int64_t grid_position(const Grid &g, int x, int y, in
 //   a* = (1 - lp)/2 (d_i + d_opp) + w_i A + rho (c.u) (4.5 lp w_i c.u + 9 (1 - lp/2) w_i c.g)
 //   b* = (1 - lm)/2 (d_i - d_opp) + rho (3 lm w_i c.u + 3 (1 - lm/2) w_i c.g)
 //   d*_0 = (1 - lp) d_0 + w_0 A
-// and for BGK d*_i = (1 - lp) d_i + (w_i A + ...) +- (...), which keeps
-// lp = 0 (no collision) an exact identity.
+// and for BGK d*_i = (1 - lp) d_i + (P +- M) with P +- M formed in one
+// chain per member (below), which keeps lp = 0 (no collision) an exact
+// identity.
 //
 // With SCALED the d_i arrive multiplied by the storage scale s (a power of
 // two, S for F16S) and leave multiplied by it; the moments are unscaled
@@ -226,6 +227,7 @@ struct CollK {
   T q15, q3;         // 1.5 lp, 3 (1 - lp/2)
   T tp[2], tm[2];    // 4.5 lp w, 3 lm w for w = 1/18, 1/36
   T fp[10], fm[10];  // pair k (odd member 2k-1): 9 (1 - lp/2) w c.g, 3 (1 - lm/2) w c.g
+  T zp[10], zm[10];  // fp_k + tm_c, fp_k - tm_c (c the weight class of pair k)
   T hg[3], g[3];     // g/2, g
   int bgk;           // lm == lp
 };
@@ -247,13 +249,15 @@ __host__ __device__ inline CollK<T> make_collk(T lp, T lm, T gx, T gy, T gz) {
     K.tp[c] = R::mul(R::mul(T(4.5), lp), w[c]);
     K.tm[c] = R::mul(R::mul(T(3), lm), w[c]);
   }
-  K.fp[0] = K.fm[0] = T(0);
+  K.fp[0] = K.fm[0] = K.zp[0] = K.zm[0] = T(0);
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;
     const T cg = R::add(R::add(R::mul(T(CX(i)), gx), R::mul(T(CY(i)), gy)), R::mul(T(CZ(i)), gz));
     const T wi = i <= 6 ? w[0] : w[1];
     K.fp[k] = R::mul(R::mul(R::mul(T(9), kp), wi), cg);
     K.fm[k] = R::mul(R::mul(R::mul(T(3), km), wi), cg);
+    K.zp[k] = R::add(K.fp[k], K.tm[i <= 6 ? 0 : 1]);
+    K.zm[k] = R::sub(K.fp[k], K.tm[i <= 6 ? 0 : 1]);
   }
   K.g[0] = gx;
   K.g[1] = gy;
@@ -320,8 +324,11 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
   const T sA = R::fma(-srho, q, R::mul(K.lp, sdrho));  // s * A
   d[0] = R::fma(K.om1, d[0], R::mul(T(WD(0)), sA));
   const T wsA[2] = {R::mul(T(WD(1)), sA), R::mul(T(WD(7)), sA)};
-  // P = s (w_i A + rho (c.u)(...)), M = s rho (...) of pair k
-  auto terms = [&](int k, T &P, T &M) {
+  // For pair k with P = s (w A + rho (c.u)(tp_c c.u + fp_k)) and
+  // M = s rho (tm_c c.u + fm_k), the two sums are formed directly:
+  //   P +- M = wsA + s rho [ (c.u) (tp_c c.u + (fp_k +- tm_c)) +- fm_k ]
+  // (without a force: wsA + (s rho c.u)(tp_c c.u +- tm_c)).
+  auto terms = [&](int k, T &Pp, T &Pm) {
     const int i = 2 * k - 1;
     const int c = i <= 6 ? 0 : 1;
     T cu = 0;
@@ -329,19 +336,25 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
     if (CX(i)) { cu = CX(i) > 0 ? ux : -ux; first = false; }
     if (CY(i)) { cu = first ? (CY(i) > 0 ? uy : -uy) : (CY(i) > 0 ? R::add(cu, uy) : R::sub(cu, uy)); first = false; }
     if (CZ(i)) { cu = first ? (CZ(i) > 0 ? uz : -uz) : (CZ(i) > 0 ? R::add(cu, uz) : R::sub(cu, uz)); }
-    const T tp = FORCE ? R::fma(K.tp[c], cu, K.fp[k]) : R::mul(K.tp[c], cu);
-    const T tm = FORCE ? R::fma(K.tm[c], cu, K.fm[k]) : R::mul(K.tm[c], cu);
-    P = R::fma(srho, R::mul(cu, tp), wsA[c]);
-    M = R::mul(srho, tm);
+    if (FORCE) {
+      const T yp = R::fma(cu, R::fma(K.tp[c], cu, K.zp[k]), K.fm[k]);
+      const T ym = R::fma(cu, R::fma(K.tp[c], cu, K.zm[k]), -K.fm[k]);
+      Pp = R::fma(srho, yp, wsA[c]);
+      Pm = R::fma(srho, ym, wsA[c]);
+    } else {
+      const T sc = R::mul(srho, cu);
+      Pp = R::fma(sc, R::fma(K.tp[c], cu, K.tm[c]), wsA[c]);
+      Pm = R::fma(sc, R::fma(K.tp[c], cu, -K.tm[c]), wsA[c]);
+    }
   };
   if (K.bgk) {
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
       const int i = 2 * k - 1;
-      T P, M;
-      terms(k, P, M);
-      d[i] = R::fma(K.om1, d[i], R::add(P, M));
-      d[i + 1] = R::fma(K.om1, d[i + 1], R::sub(P, M));
+      T Pp, Pm;
+      terms(k, Pp, Pm);
+      d[i] = R::fma(K.om1, d[i], Pp);
+      d[i + 1] = R::fma(K.om1, d[i + 1], Pm);
     }
   } else {
     // a* +- b* with a = (d_i + d_opp)/2, b = (d_i - d_opp)/2 expanded, so
@@ -350,11 +363,11 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
       const int i = 2 * k - 1;
-      T P, M;
-      terms(k, P, M);
+      T Pp, Pm;
+      terms(k, Pp, Pm);
       const T di = d[i], dj = d[i + 1];
-      d[i] = R::fma(K.al, di, R::fma(K.be, dj, R::add(P, M)));
-      d[i + 1] = R::fma(K.al, dj, R::fma(K.be, di, R::sub(P, M)));
+      d[i] = R::fma(K.al, di, R::fma(K.be, dj, Pp));
+      d[i + 1] = R::fma(K.al, dj, R::fma(K.be, di, Pm));
     }
   }
 }
@@ -381,6 +394,7 @@ struct StepParams {
   const int32_t *idx; // indirect: IDX (18 x ipad) or the esoteric twist's packed 9 x ipad
   int64_t ipad;
   int map[Q];         // esoteric twist: physical array of direction i
+  void *mapbase[Q];   // esoteric twist, SoA: start of array map[i] (A + map[i] npad)
   double omega, gx, gy, gz;
   double omega_m;     // antisymmetric rate (TRT); equal to omega for BGK
   CollK<float> kf;    // collision constants for FP32 arithmetic (F32, F16S)

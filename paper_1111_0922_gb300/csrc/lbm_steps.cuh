@@ -291,19 +291,32 @@ template <bool FAST, class C, int AOS, bool IND, bool FORCE>
 __device__ __forceinline__ void et_node(const StepParams &p, NodeOf<IND> &nd, const Lattice<C, AOS> &A, double &m,
                                         double &j) {
   using T = typename C::T;
+  using S = typename C::S;
+  // array map[k] at slot pos: SoA through the per-array start pointers
+  auto ld = [&](int k, int pos) -> T {
+    if constexpr (AOS == 0) return C::raw(static_cast<const S *>(p.mapbase[k])[pos]);
+    return A.ld(p.map[k], pos);
+  };
+  // store into array map[ka] if `first`, else map[kb] (ka, kb compile-time)
+  auto st = [&](bool first, int ka, int kb, int pos, T v) {
+    if constexpr (AOS == 0)
+      static_cast<S *>(first ? p.mapbase[ka] : p.mapbase[kb])[pos] = C::unraw(v);
+    else
+      A.st(first ? p.map[ka] : p.map[kb], pos, v);
+  };
   uint32_t w[10];  // packed index words (IDX addressing), kept across the collision
   if (IND) {
 #pragma unroll
     for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.ipad + nd.s);
   }
   T d[Q];
-  d[0] = A.ld(p.map[0], nd.s);
+  d[0] = ld(0, nd.s);
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;
-    d[i] = A.ld(p.map[i], nd.s);
+    d[i] = ld(i, nd.s);
     const int pos = IND ? (int)(w[k] & 0x7fffffffu) : et_pos(nd, p, i);
-    d[i + 1] = A.ld(p.map[i + 1], pos);
+    d[i + 1] = ld(i + 1, pos);
   }
   run_collision<C, FORCE>(d, p, m, j);
   nd.launder_all();
@@ -311,7 +324,7 @@ __device__ __forceinline__ void et_node(const StepParams &p, NodeOf<IND> &nd, co
 #pragma unroll
     for (int k = 1; k <= 9; ++k) w[k] = (uint32_t)launder((int)w[k]);
   }
-  A.st(p.map[0], nd.s, d[0]);
+  st(true, 0, 0, nd.s, d[0]);
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int i = 2 * k - 1;
@@ -327,8 +340,8 @@ __device__ __forceinline__ void et_node(const StepParams &p, NodeOf<IND> &nd, co
       lm = FAST || et_linked(nd, p, i + 1);
     }
     // odd direction i: to x + c_i; even direction i+1: to x itself
-    A.st(lp ? p.map[i + 1] : p.map[i], pos, d[i]);
-    A.st(lm ? p.map[i] : p.map[i + 1], nd.s, d[i + 1]);
+    st(lp, i + 1, i, pos, d[i]);
+    st(lm, i, i + 1, nd.s, d[i + 1]);
   }
 }
 
