@@ -85,18 +85,19 @@ def roof_mflups(variant: str, indirect: bool, precision: str, hbm_gbs: float) ->
 
 # FP64 instruction roof on GB300: 2 FP64 thread-instructions per clock per SM
 # (ncu's sm__sass_thread_inst_executed_op_dfma_pred_on peak) on 152 SMs at the
-# 2.07 GHz maximum SM clock.  The BGK collision issues about 143 FP64
-# instructions per update without a body force (ncu, AA pattern on 256^3);
-# counted from the source, a force adds 7 (u, u.g) and TRT adds 18 (two more
-# operations per opposite pair).
+# 2.07 GHz maximum SM clock.  The BGK collision issues 127 FP64 instructions
+# per update without a body force (ncu, AA pattern on 256^3: 46 DADD, 63
+# DFMA, 18 DMUL per node); counted from the source, a force adds 16 (u, u.g,
+# one more operation per opposite pair) and TRT adds 18 (two more operations
+# per opposite pair).
 FP64_INST_PER_CLK_SM = 2
 GB300_SMS = 152
 GB300_SM_GHZ = 2.07
-FP64_INST_BGK = 143
+FP64_INST_BGK = 127
 
 
 def fp64_inst_per_flup(force: bool = False, trt: bool = False) -> int:
-    return FP64_INST_BGK + (7 if force else 0) + (18 if trt else 0)
+    return FP64_INST_BGK + (16 if force else 0) + (18 if trt else 0)
 
 
 def fp64_roof_mflups(force: bool = False, trt: bool = False) -> float:

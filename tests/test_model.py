@@ -51,9 +51,9 @@ def test_gpu_model_values():
 def test_fp64_pipe_roof():
     from paper_1111_0922_gb300 import model
 
-    # 2 FP64 instructions per clock per SM x 152 SMs x 2.07 GHz / 143 per update
-    assert abs(model.fp64_roof_mflups() - 2 * 152 * 2.07e9 / 143 / 1e6) < 1e-6
-    assert model.fp64_inst_per_flup(True, True) == 143 + 7 + 18
+    # 2 FP64 instructions per clock per SM x 152 SMs x 2.07 GHz / 127 per update
+    assert abs(model.fp64_roof_mflups() - 2 * 152 * 2.07e9 / 127 / 1e6) < 1e-6
+    assert model.fp64_inst_per_flup(True, True) == 127 + 16 + 18
     bound, roof = model.bound_roof("aa", False, "f64", 6780.0)
     assert bound == "alu" and roof < model.roof_mflups("aa", False, "f64", 6780.0)
     assert model.bound_roof("aa", False, "f32", 6780.0)[0] == "hbm"
