@@ -239,7 +239,10 @@ static StepParams params_of(const lbm_t *h) {
 static LaunchShape shape_of(const lbm_t *h) {
   LaunchShape L;
   const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
-  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
+  // full grids: two planes per thread by default (measured +2 % FP32, +5 %
+  // FP16 on 256^3); node lists: one node per thread
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread
+                                               : (h->cfg.addressing == LBM_DIRECT ? 2 : 1);
   if (h->cfg.addressing == LBM_DIRECT) {
     const int bx = (int)std::min<int64_t>(bs, round_up(h->cfg.nx, 32));
     const int by = std::max(1, bs / bx);
