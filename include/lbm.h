@@ -95,7 +95,8 @@ typedef struct lbm_config {
   double trt_magic;          /* 0 = BGK; > 0 = two-relaxation-time collision with magic parameter
                                 Lam = (1/omega - 1/2)(1/omega_minus - 1/2), e.g. 3/16 (walls exactly
                                 half-way for Poiseuille flow) */
-  int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128 */
+  int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128
+                                (256 for LBM_AA on a node list) */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default (full grid: 2 planes;
                                 node list: 1 node) */
   int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes);
