@@ -999,8 +999,9 @@ static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
     }
     p.z0 = z0;
     p.z1 = z1;
-    LaunchShape L = shape_of(h);
-    L.grid.z = (unsigned)std::min<int64_t>(z1 - z0, 65535);
+    LaunchShape L = shape_of(h);  // its grid z covers nz with the planes per thread; refit to the slab
+    const int npt = (h->cfg.nz + (int)L.grid.z - 1) / std::max(1, (int)L.grid.z);
+    L.grid.z = (unsigned)std::min<int64_t>((z1 - z0 + npt - 1) / npt, 65535);
     p.partials = h->d_partials + 2 * used;
     launch_step_kernel_cg(p, k, L);
     used += (int)blocks_of(L);
