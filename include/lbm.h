@@ -99,8 +99,9 @@ typedef struct lbm_config {
                                 (256 for LBM_AA on a node list) */
   int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default (full grid: 2 planes;
                                 node list: 1 node) */
-  int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes);
-                                node list: slab size B >= 1 nodes; 0 = default */
+  int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes, k extra
+                                planes of storage; 0 = slabs of about 2^22 cells);
+                                node list: slab size B >= 1 nodes (0 = 2^21) */
   int32_t pair_x;            /* LBM_AA, full grid, SoA: 1 = two x-adjacent nodes per thread with vector
                                 accesses where possible (periodic x, even nx, no solid cell);
                                 0 = one node per thread (default, faster on GB300) */
