@@ -70,6 +70,10 @@ struct SwapTiles {
   int ncolours;
 };
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
+// two-pass schedule: all tiles (own links), then the links between tiles
+// (one thread per cell on face_grid x face_block, z planes strided by grid z)
+void launch_swap_two_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, dim3 face_grid, dim3 face_block,
+                          cudaStream_t s);
 // the same pass with tensor-copy staging (full grid, SoA, strides multiple of
 // 16 bytes); `map` describes the lattice as a 4D tensor (x, y, z, array) with
 // the tile as its box.  Launches persistent blocks (as many as are resident

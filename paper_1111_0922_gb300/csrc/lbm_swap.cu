@@ -13,6 +13,9 @@ extern template void swap_pass_t<CodecF32>(const StepParams &, const SwapPass &,
                                            cudaStream_t);
 extern template void swap_pass_t<CodecF16S>(const StepParams &, const SwapPass &, const KernelKey &, size_t,
                                             cudaStream_t);
+extern template void swap_faces_t<CodecF64>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
+extern template void swap_faces_t<CodecF32>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
+extern template void swap_faces_t<CodecF16S>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
 extern template int swap_pass_tma_t<CodecF64>(const StepParams &, const SwapPass &, const KernelKey &,
                                               const CUtensorMap *, int, int, cudaStream_t);
 extern template int swap_pass_tma_t<CodecF32>(const StepParams &, const SwapPass &, const KernelKey &,
@@ -76,7 +79,33 @@ static SwapPass pass_of(const StepParams &p, const SwapTiles &t) {
   axis_set(t.ntx, p.g.px, c0, sp.start[0], sp.count[0]);
   axis_set(t.nty, p.g.py, c1, sp.start[1], sp.count[1]);
   axis_set(t.ntz, p.g.pz, c2, sp.start[2], sp.count[2]);
+  sp.stride = 2;
   return sp;
+}
+
+// Two-pass schedule (see k_swap_faces): first every tile in one launch,
+// completing only its own links (colour 0 for all, so no neighbour counts as
+// earlier), then the pass over the links between tiles.
+void launch_swap_two_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, dim3 face_grid, dim3 face_block,
+                          cudaStream_t s) {
+  SwapPass sp = pass_of(p, t);
+  sp.colour = 0;
+  sp.start[0] = sp.start[1] = sp.start[2] = 0;
+  sp.count[0] = t.ntx;
+  sp.count[1] = t.nty;
+  sp.count[2] = t.ntz;
+  sp.stride = 1;
+  const size_t smem = swap_smem_bytes(t, k.precision);
+  if (k.precision == 0) {
+    swap_pass_t<CodecF64>(p, sp, k, smem, s);
+    swap_faces_t<CodecF64>(p, sp, k.aos, face_grid, face_block, s);
+  } else if (k.precision == 1) {
+    swap_pass_t<CodecF32>(p, sp, k, smem, s);
+    swap_faces_t<CodecF32>(p, sp, k.aos, face_grid, face_block, s);
+  } else {
+    swap_pass_t<CodecF16S>(p, sp, k, smem, s);
+    swap_faces_t<CodecF16S>(p, sp, k.aos, face_grid, face_block, s);
+  }
 }
 
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s) {

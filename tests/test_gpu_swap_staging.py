@@ -27,7 +27,7 @@ def L():
 
 
 def _run(L, dims, per, precision, staging, solid, f0, steps, omega, g):
-    lat = L.Lattice(dims, per, variant="swap", precision=precision, omega=omega, force=g, tile_staging=staging)
+    lat = L.Lattice(dims, per, variant="swap", precision=precision, omega=omega, force=g, swap_schedule=staging)
     lat.set_geometry(solid)
     lat.set_pdfs(f0)
     lat.step(steps)
@@ -46,10 +46,12 @@ def test_staged_swap_equals_plain_and_oracle(L, precision, dims, per):
     solid = (rng.random(n) < 0.1).astype(np.uint8)
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     g = (2e-5, 1e-5, -5e-6)
-    a, sa = _run(L, dims, per, precision, 1, solid, f0, 6, 1.2, g)
-    b, sb = _run(L, dims, per, precision, 0, solid, f0, 6, 1.2, g)
-    assert sa == 1 and sb == 0
+    a, sa = _run(L, dims, per, precision, 2, solid, f0, 6, 1.2, g)
+    b, sb = _run(L, dims, per, precision, 1, solid, f0, 6, 1.2, g)
+    c, sc = _run(L, dims, per, precision, 0, solid, f0, 6, 1.2, g)
+    assert sa == 1 and sb == 0 and sc == 0
     assert np.array_equal(a, b)
+    assert np.array_equal(a, c)  # the same arithmetic per node, exact moves
     ref = oracle.run_push(dims, per, solid, f0, 6, 1.2, g)
     fl = solid == 0
     if precision == "f64":
@@ -62,7 +64,7 @@ def test_staged_swap_equals_plain_and_oracle(L, precision, dims, per):
 
 def test_rows_off_the_16_byte_grid_use_plain_loads(L):
     # FP32 rows of 70 cells are 280 bytes: no tensor copies
-    lat = L.Lattice((70, 8, 4), (1, 1, 1), variant="swap", precision="f32", tile_staging=1)
+    lat = L.Lattice((70, 8, 4), (1, 1, 1), variant="swap", precision="f32", swap_schedule=2)
     lat.set_geometry(None)
     assert lat.info.tile_staged == 0
     lat.close()
@@ -85,7 +87,7 @@ def test_bounded_wait_gives_up_and_context_survives(L):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("staging", [0, 1])
+@pytest.mark.parametrize("staging", [0, 1, 2])
 @pytest.mark.parametrize("per", [(1, 1, 1), (1, 0, 1), (0, 0, 0), (0, 1, 1)])
 @pytest.mark.parametrize("dims", [(64, 8, 6), (96, 12, 8), (72, 9, 5)])
 def test_swap_without_solids_matches_oracle(L, dims, per, staging):
@@ -97,7 +99,7 @@ def test_swap_without_solids_matches_oracle(L, dims, per, staging):
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     g = (1e-5, -2e-5, 3e-6)
     ref = oracle.run_push(dims, per, None, f0, 5, 1.3, g)
-    lat = L.Lattice(dims, per, variant="swap", precision="f64", omega=1.3, force=g, tile_staging=staging)
+    lat = L.Lattice(dims, per, variant="swap", precision="f64", omega=1.3, force=g, swap_schedule=staging)
     lat.set_geometry(None)
     lat.set_pdfs(f0)
     lat.step(5)
