@@ -108,12 +108,14 @@ typedef struct lbm_config {
   int32_t store_hint;        /* LBM_OS_PUSH / LBM_OS_PULL, SoA: 1 = write the second lattice with
                                 cache-streaming (evict-first) stores, the GPU counterpart of the
                                 non-temporal stores of OS-NT (Sec. 3); 0 = ordinary stores */
-  int32_t swap_schedule;     /* LBM_SWAP, full grid: 0 = two passes per step: every tile collides and
-                                completes its own links, then one pass completes the links between
-                                tiles (default, fastest on GB300); 1 = coloured passes: tiles of one
-                                colour per pass, links to earlier colours completed in place;
-                                2 = coloured passes with each tile staged by one tensor copy (TMA)
-                                in persistent blocks (SoA, row pitch a multiple of 16 bytes) */
+  int32_t swap_schedule;     /* LBM_SWAP, full grid: 1 = coloured passes: tiles of one colour per
+                                pass, links to tiles of earlier colours completed in place;
+                                2 = the same with each tile staged by one tensor copy (TMA) in
+                                persistent blocks (SoA, row pitch a multiple of 16 bytes);
+                                3 = two passes per step: every tile collides and completes its own
+                                links, then one pass completes the links between tiles;
+                                0 = default: 2 for FP32/FP16 storage where allowed, else 1
+                                (measured fastest on GB300) */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

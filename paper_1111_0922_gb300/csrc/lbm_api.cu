@@ -379,8 +379,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
   if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint = 1 needs LBM_OS_PUSH or LBM_OS_PULL with LBM_SOA");
-  if (cfg->swap_schedule < 0 || cfg->swap_schedule > 2)
-    return fail(nullptr, LBM_ERR_INVALID_ARG, "swap_schedule must be 0, 1 or 2");
+  if (cfg->swap_schedule < 0 || cfg->swap_schedule > 3)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "swap_schedule must be 0 .. 3");
 
   lbm_t *h = new lbm_t();
   h->cfg = *cfg;
@@ -573,7 +573,8 @@ static lbm_status build_geometry(lbm_t *h) {
     h->idx_folded = true;
   }
   h->swap_tma = false;
-  if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA && c.swap_schedule == 2) {
+  if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA &&
+      (c.swap_schedule == 2 || (c.swap_schedule == 0 && c.precision != LBM_F64))) {
     // tensor copies need 16-byte row pitches and inner box extents
     const SwapTiles t = swap_tiles(h);
     const cuuint64_t es = (cuuint64_t)store_size(c.precision);
@@ -750,7 +751,7 @@ static int kernels_per_step(const lbm_t *h) {
       return (h->cfg.nz + slab - 1) / slab + (h->cfg.periodic[2] ? 1 : 0);
     }
     case LBM_SWAP:
-      return (h->cfg.addressing == LBM_INDIRECT || h->cfg.swap_schedule == 0) ? 2 : swap_tiles(h).ncolours;
+      return (h->cfg.addressing == LBM_INDIRECT || h->cfg.swap_schedule == 3) ? 2 : swap_tiles(h).ncolours;
     default: return 1;
   }
 }
@@ -1029,7 +1030,7 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
     return LBM_OK;
   }
   SwapTiles t = swap_tiles(h);
-  if (h->cfg.swap_schedule == 0) {
+  if (h->cfg.swap_schedule == 3) {
     const LaunchShape L = shape_of(h);
     p.partials = h->d_partials;
     launch_swap_two_pass(p, t, k, L.grid, L.block, h->stream);

@@ -92,7 +92,7 @@ def main(argv=None):
     ap.add_argument("--store-hint", type=int, default=0,
                     help="OS push/pull, SoA: 1 = cache-streaming stores of the second lattice (OS-NT analogue)")
     ap.add_argument("--swap-schedule", type=int, default=0,
-                    help="swap, full grid: 0 = two passes, 1 = coloured passes, 2 = coloured with tensor-copy staging")
+                    help="swap, full grid: 0 default, 1 coloured passes, 2 coloured with tensor-copy staging, 3 two passes")
     ap.add_argument("--trt", action="store_true", help="two-relaxation-time collision, magic 3/16")
     args = ap.parse_args(argv)
     import torch
