@@ -57,6 +57,9 @@ struct lbm {
   alignas(64) CUtensorMap swap_map{};
   bool swap_tma = false;
   int nsm = 0;
+  // swap on a full grid: per-tile link-class tables (coloured and two-pass)
+  uint16_t *d_swap_tcls = nullptr, *d_swap_tcls_all = nullptr;
+  uint32_t *d_swap_tables = nullptr, *d_swap_tables_all = nullptr;
 };
 
 static std::string g_last_error;
@@ -296,6 +299,10 @@ static SwapTiles swap_tiles(const lbm_t *h) {
   t.ntz = (h->cfg.nz + t.tz - 1) / t.tz;
   t.colour = 0;
   t.ncolours = swap_colours(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]);
+  t.tcls = h->d_swap_tcls;
+  t.tables = h->d_swap_tables;
+  t.tcls_all = h->d_swap_tcls_all;
+  t.tables_all = h->d_swap_tables_all;
   return t;
 }
 
@@ -600,6 +607,23 @@ static lbm_status build_geometry(lbm_t *h) {
       h->nsm = nsm;
     }
   }
+  if (c.variant == LBM_SWAP && !ind) {
+    const SwapTiles t = swap_tiles(h);
+    for (int all = 0; all < 2; ++all) {
+      std::vector<uint16_t> tcls;
+      std::vector<uint32_t> tables;
+      build_swap_tables(t, c.periodic, all == 1, tcls, tables);
+      uint16_t *dt = static_cast<uint16_t *>(dalloc(h, sizeof(uint16_t) * tcls.size(), h->geo_allocs));
+      uint32_t *dtab = static_cast<uint32_t *>(dalloc(h, sizeof(uint32_t) * tables.size(), h->geo_allocs));
+      if (!dt || !dtab) return fail(h, LBM_ERR_OOM, "swap link-class tables");
+      CUDA_TRY(h, cudaMemcpyAsync(dt, tcls.data(), sizeof(uint16_t) * tcls.size(), cudaMemcpyHostToDevice, h->stream));
+      CUDA_TRY(h, cudaMemcpyAsync(dtab, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice,
+                                  h->stream));
+      CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+      (all ? h->d_swap_tcls_all : h->d_swap_tcls) = dt;
+      (all ? h->d_swap_tables_all : h->d_swap_tables) = dtab;
+    }
+  }
   // reduction partials: enough for a step launch and for the read-out kernel
   const LaunchShape L = shape_of(h);
   int64_t need = std::max<int64_t>(blocks_of(L), reduce_blocks_for(h->nn));
@@ -631,6 +655,8 @@ static void reset_geometry(lbm_t *h) {
   h->nodes = h->nghost = h->nn = h->slots = h->npad = h->ipad = 0;
   h->idx_folded = false;
   h->swap_tma = false;
+  h->d_swap_tcls = h->d_swap_tcls_all = nullptr;
+  h->d_swap_tables = h->d_swap_tables_all = nullptr;
   h->steps = 0;
   for (int i = 0; i < Q; ++i) h->map[i] = i;
 }

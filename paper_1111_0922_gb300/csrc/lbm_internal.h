@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "lbm_core.cuh"
 
@@ -68,7 +69,17 @@ struct SwapTiles {
   int ntx, nty, ntz;    // tiles per axis
   int colour;           // pass being run
   int ncolours;
+  // link-class tables (built once per geometry): per tile (x fastest) the
+  // index of its table; a table is 2 + 3 x 18 words: the earlier-colour and
+  // self neighbour masks of the 27 tile offsets, then for each of the 18
+  // cell classes of a full tile the outside / remote / self link masks.
+  // *_all: the same for the two-pass schedule (no tile counts as earlier).
+  const uint16_t *tcls = nullptr, *tcls_all = nullptr;
+  const uint32_t *tables = nullptr, *tables_all = nullptr;
 };
+constexpr int kSwapTableWords = 2 + 3 * 18;
+void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, std::vector<uint16_t> &tcls,
+                       std::vector<uint32_t> &tables);
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
 // two-pass schedule: all tiles (own links), then the links between tiles
 // (one thread per cell on face_grid x face_block, z planes strided by grid z)

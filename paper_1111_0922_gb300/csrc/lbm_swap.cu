@@ -1,6 +1,10 @@
 // Host side of the swap scheme (Sec. 5): pass bookkeeping for the blocked
 // full-grid swap (kernels in lbm_swap.cuh), the node-list link exchange, and
 // the bounded-wait self-test.
+#include <map>
+#include <utility>
+#include <vector>
+
 #include "../../include/lbm.h"
 #include "lbm_swap.cuh"
 
@@ -34,6 +38,90 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
 }
 
 // tiles are at most 32 x 4 x 2 = 256 cells (one thread each)
+// ---------------------------------------------------------------------------
+// Link-class tables of the tiles (see SwapTiles).  A tile's colour is fixed
+// by its per-axis colours; a neighbour at offset o is "earlier" when its
+// colour index is lower (its pass ran first) and "self" when the tile wraps
+// onto itself across a periodic face.
+static int axis_colour_host(int t, int nt, int periodic) {
+  if (nt == 1) return 0;
+  if (periodic && (nt & 1)) return t == nt - 1 ? 2 : (t & 1);
+  return t & 1;
+}
+
+void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, std::vector<uint16_t> &tcls,
+                       std::vector<uint32_t> &tables) {
+  auto ncol = [](int nt, int periodic) { return nt == 1 ? 1 : ((periodic && (nt & 1)) ? 3 : 2); };
+  const int nt[3] = {t.ntx, t.nty, t.ntz};
+  const int cx = ncol(t.ntx, per[0]), cy = ncol(t.nty, per[1]);
+  auto colour = [&](const int a[3]) {
+    return axis_colour_host(a[0], nt[0], per[0]) +
+           cx * (axis_colour_host(a[1], nt[1], per[1]) + cy * axis_colour_host(a[2], nt[2], per[2]));
+  };
+  std::map<std::pair<uint32_t, uint32_t>, int> seen;
+  tcls.assign((size_t)nt[0] * nt[1] * nt[2], 0);
+  tables.clear();
+  for (int tz = 0; tz < nt[2]; ++tz)
+    for (int ty = 0; ty < nt[1]; ++ty)
+      for (int tx = 0; tx < nt[0]; ++tx) {
+        const int tile[3] = {tx, ty, tz};
+        const int own = colour(tile);
+        uint32_t em = 0, sm = 0;
+        for (int l = 0; l < 27; ++l) {
+          const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, l / 9 - 1};
+          int nb[3];
+          bool exists = true, self = true;
+          for (int a = 0; a < 3; ++a) {
+            nb[a] = tile[a] + o[a];
+            if (nb[a] < 0 || nb[a] >= nt[a]) {
+              if (!per[a]) exists = false;
+              nb[a] = (nb[a] + nt[a]) % nt[a];
+            }
+            self = self && nb[a] == tile[a];
+          }
+          if (!exists) continue;
+          if (self)
+            sm |= 1u << l;
+          else if (!none_earlier && colour(nb) < own)
+            em |= 1u << l;
+        }
+        auto key = std::make_pair(em, sm);
+        auto it = seen.find(key);
+        int index;
+        if (it == seen.end()) {
+          index = (int)seen.size();
+          seen[key] = index;
+          tables.push_back(em);
+          tables.push_back(sm);
+          // cell classes of a full 32 x 4 x 2 tile: x low/inner/high,
+          // y low/inner/high, z low/high
+          for (int c = 0; c < 18; ++c) {
+            const int xc = c % 3, yc = (c / 3) % 3, zc = c / 9;
+            uint32_t om = 0, rm = 0, smk = 0;
+            for (int i = 1; i < Q; ++i) {
+              const int ci[3] = {CX(i), CY(i), CZ(i)};
+              const bool ox = ci[0] > 0 ? xc == 0 : (ci[0] < 0 ? xc == 2 : false);
+              const bool oy = ci[1] > 0 ? yc == 0 : (ci[1] < 0 ? yc == 2 : false);
+              const bool oz = ci[2] > 0 ? zc == 0 : (ci[2] < 0 ? zc == 1 : false);
+              if (!(ox || oy || oz)) continue;
+              om |= 1u << i;
+              const int bit = tile_bit(ox ? -ci[0] : 0, oy ? -ci[1] : 0, oz ? -ci[2] : 0);
+              if (sm & (1u << bit))
+                smk |= 1u << i;
+              else if (em & (1u << bit))
+                rm |= 1u << i;
+            }
+            tables.push_back(om);
+            tables.push_back(rm);
+            tables.push_back(smk);
+          }
+        } else {
+          index = it->second;
+        }
+        tcls[tx + (size_t)nt[0] * (ty + (size_t)nt[1] * tz)] = (uint16_t)index;
+      }
+}
+
 // S (19 post-collision PDFs per cell, compute type) and the remote-prefetch
 // buffer (18 words per cell, the stored element or its 4-byte word)
 size_t swap_smem_bytes(const SwapTiles &t, int precision) {
@@ -80,6 +168,8 @@ static SwapPass pass_of(const StepParams &p, const SwapTiles &t) {
   axis_set(t.nty, p.g.py, c1, sp.start[1], sp.count[1]);
   axis_set(t.ntz, p.g.pz, c2, sp.start[2], sp.count[2]);
   sp.stride = 2;
+  sp.tcls = t.tcls;
+  sp.tables = t.tables;
   return sp;
 }
 
@@ -95,6 +185,8 @@ void launch_swap_two_pass(const StepParams &p, const SwapTiles &t, const KernelK
   sp.count[1] = t.nty;
   sp.count[2] = t.ntz;
   sp.stride = 1;
+  sp.tcls = t.tcls_all;
+  sp.tables = t.tables_all;
   const size_t smem = swap_smem_bytes(t, k.precision);
   if (k.precision == 0) {
     swap_pass_t<CodecF64>(p, sp, k, smem, s);

@@ -36,7 +36,16 @@ struct SwapPass {
   int colour;                  // colour of this pass (cx-fastest)
   int start[3], count[3];      // tiles of this pass per axis: start + stride k
   int stride;                  // 2 for a colour of the coloured schedule; 1 for every tile at once
+  const uint16_t *tcls;        // per tile: index of its link-class table
+  const uint32_t *tables;      // kSwapTableWords words per table
 };
+
+// The link-class table of a tile (built on the host): [0] earlier-colour
+// neighbour mask, [1] self mask, [2 + 3c ...] the class words of cell class c.
+__device__ __forceinline__ const uint32_t *tile_table(const SwapPass &sp, const int tile[3]) {
+  const int tl = tile[0] + sp.ntx * (tile[1] + sp.nty * tile[2]);
+  return sp.tables + kSwapTableWords * (int)__ldg(sp.tcls + tl);
+}
 
 // full tile box (cells): 32 along x (one warp per row), 4 along y, 2 along z
 constexpr int kSwapTX = 32, kSwapTY = 4, kSwapTZ = 2;
@@ -49,80 +58,6 @@ __device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
 
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
-
-// Classify one of the 27 tile offsets l (o = (l%3 - 1, (l/3)%3 - 1, l/9 - 1),
-// so l = tile_bit(o)) of `tile` for this pass: `earlier` when that neighbour
-// exists and has an earlier colour, `self` when the tile is its own neighbour
-// across a periodic face.  The threads of a block take the offsets in
-// parallel and OR the bits together in shared memory.
-__device__ __forceinline__ void classify_offset(const Grid &g, const SwapPass &sp, const int tile[3], int l,
-                                                bool &earlier, bool &self) {
-  const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, l / 9 - 1};
-  const int nt[3] = {sp.ntx, sp.nty, sp.ntz};
-  const int per[3] = {g.px, g.py, g.pz};
-  bool exists = true;
-  self = true;
-  int nb[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    nb[a] = tile[a] + o[a];
-    if (nb[a] < 0 || nb[a] >= nt[a]) {
-      if (!per[a]) exists = false;
-      nb[a] = (nb[a] + nt[a]) % nt[a];
-    }
-    self = self && nb[a] == tile[a];
-  }
-  const int col = axis_colour(nb[0], nt[0], per[0]) +
-                  sp.cx * (axis_colour(nb[1], nt[1], per[1]) + sp.cy * axis_colour(nb[2], nt[2], per[2]));
-  earlier = exists && !self && col < sp.colour;
-  self = exists && self;
-}
-
-__device__ __forceinline__ void classify_into(const Grid &g, const SwapPass &sp, const int tile[3], int t, int nthreads,
-                                              unsigned *em, unsigned *sm) {
-  for (int l = t; l < 27; l += nthreads) {
-    bool e, f;
-    classify_offset(g, sp, tile, l, e, f);
-    if (e) atomicOr(em, 1u << l);
-    if (f) atomicOr(sm, 1u << l);
-  }
-}
-
-// One tile, all threads of the block (thread (lx, ly, lz) owns cell
-// org + (lx, ly, lz)).  Phase 1: every node collides; its post-collision
-// PDFs go to S[i * TN + t] (S in shared memory).  The node's stored PDFs
-// come from global memory, or from `stage` (the tile as the tensor copy left
-// it in shared memory, same layout; it may alias S).  Phase 2: each node
-// gathers the PDFs that end in its slots and writes them, and completes its
-// links to tiles of earlier colours in global memory.
-// Link classes of a full 32 x 4 x 2 tile.  A cell's links depend only on
-// which faces it lies on: x low / inner / high, y low / inner / high, z low /
-// high, 18 cell classes c = xc + 3 (yc + 3 zc).  For each class and
-// direction i (bit i) the table holds: [0] the source x - c_i lies outside
-// the tile, [1] ... in a tile of an earlier colour (a remote exchange),
-// [2] ... in the tile itself across a periodic face.  Threads t < 18 fill it.
-__device__ __forceinline__ void build_class_table(unsigned em, unsigned sm, int t, unsigned *cls) {
-  if (t >= 18) return;
-  const int xc = t % 3, yc = (t / 3) % 3, zc = t / 9;
-  unsigned om = 0, rm = 0, smk = 0;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int cx = CX(i), cy = CY(i), cz = CZ(i);
-    const bool ox = cx > 0 ? xc == 0 : (cx < 0 ? xc == 2 : false);
-    const bool oy = cy > 0 ? yc == 0 : (cy < 0 ? yc == 2 : false);
-    const bool oz = cz > 0 ? zc == 0 : (cz < 0 ? zc == 1 : false);
-    if (!(ox || oy || oz)) continue;
-    om |= 1u << i;
-    const int bit = tile_bit(ox ? -cx : 0, oy ? -cy : 0, oz ? -cz : 0);
-    if (sm & (1u << bit))
-      smk |= 1u << i;
-    else if (em & (1u << bit))
-      rm |= 1u << i;
-  }
-  cls[3 * t] = om;
-  cls[3 * t + 1] = rm;
-  cls[3 * t + 2] = smk;
-}
 
 // FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
 // size), so shared-memory offsets are compile-time constants.
@@ -199,7 +134,7 @@ __device__ __forceinline__ typename C::T fetch_remote(const RemoteWord<C> &w, in
 
 template <class C, int AOS, bool FORCE, bool FIXED>
 __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &sp, typename C::T *S,
-                                          const typename C::S *stage, RemoteWord<C> *R, const unsigned *cls,
+                                          const typename C::S *stage, RemoteWord<C> *R, const uint32_t *cls,
                                           const int org[3], unsigned em, unsigned sm, double &m, double &jsum) {
   using T = typename C::T;
   Lattice<C, AOS> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
@@ -232,9 +167,9 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
   unsigned omask = 0, rmask = 0, smask = 0;
   if (FIXED && tile_fast && active) {
     const int c = (xm ? 0 : (xp ? 2 : 1)) + 3 * ((ym ? 0 : (yp ? 2 : 1)) + 3 * (zm ? 0 : 1));
-    omask = cls[3 * c];
-    rmask = cls[3 * c + 1];
-    smask = cls[3 * c + 2];
+    omask = __ldg(cls + 3 * c);
+    rmask = __ldg(cls + 3 * c + 1);
+    smask = __ldg(cls + 3 * c + 2);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
       if (rmask & (1u << i)) prefetch_remote<C>(&R[(i - 1) * TN + t], L.at(OPP(i), nd.nb_fast(p, OPP(i))));
@@ -347,22 +282,12 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, 
   T *S = reinterpret_cast<T *>(smem_raw);
   const int TN = sp.tx * sp.ty * sp.tz;
   RemoteWord<C> *R = reinterpret_cast<RemoteWord<C> *>(smem_raw + ((size_t)Q * TN * sizeof(T) + 15) / 16 * 16);
-  __shared__ unsigned earlier_mask, self_mask;
-  __shared__ unsigned cls[54];
   const int tile[3] = {sp.start[0] + sp.stride * (int)blockIdx.x, sp.start[1] + sp.stride * (int)blockIdx.y,
                        sp.start[2] + sp.stride * (int)blockIdx.z};
   const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
-  const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  if (t == 0) earlier_mask = self_mask = 0u;
-  __syncthreads();
-  classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &earlier_mask, &self_mask);
-  __syncthreads();
-  if (FIXED) {
-    build_class_table(earlier_mask, self_mask, t, cls);
-    __syncthreads();
-  }
+  const uint32_t *tab = tile_table(sp, tile);
   double m = 0.0, jsum = 0.0;
-  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, R, cls, org, earlier_mask, self_mask, m, jsum);
+  swap_tile<C, AOS, FORCE, FIXED>(p, sp, S, nullptr, R, tab + 2, org, __ldg(tab), __ldg(tab + 1), m, jsum);
   if (RED) block_reduce_store(m, jsum, p.partials);
 }
 
@@ -382,8 +307,6 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
   constexpr bool kInPlace = sizeof(T) == sizeof(S);  // F32, F64: collide into the staged buffer
   extern __shared__ __align__(128) unsigned char smem_tma[];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ unsigned masks[2][2];  // [buffer][earlier, self]
-  __shared__ unsigned cls[54];
   __shared__ int tiles[2][3];       // [buffer] tile coordinates, written with the copy's issue
   const int TN = sp.tx * sp.ty * sp.tz;
   const size_t stage_bytes = (size_t)Q * TN * sizeof(S);
@@ -415,7 +338,6 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    masks[0][0] = masks[0][1] = masks[1][0] = masks[1][1] = 0u;
   }
   __syncthreads();
   double m = 0.0, jsum = 0.0;
@@ -435,12 +357,6 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
         issue(n + G, b ^ 1);
       }
     }
-    // (the bits of this buffer were cleared when it was last used)
-    classify_into(p.g, sp, tile, t, blockDim.x * blockDim.y * blockDim.z, &masks[b][0], &masks[b][1]);
-    if (FIXED) {
-      __syncthreads();
-      build_class_table(masks[b][0], masks[b][1], t, cls);  // published by the vote below
-    }
     const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitNs);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
@@ -453,10 +369,8 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, S
     }
     const int org[3] = {tile[0] * sp.tx, tile[1] * sp.ty, tile[2] * sp.tz};
     T *Sbuf = kInPlace ? reinterpret_cast<T *>(stage[b]) : Sx;
-    const unsigned em = masks[b][0], sm = masks[b][1];
-    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], R, cls, org, em, sm, m, jsum);
-    // every thread read this buffer's bits before the barrier inside swap_tile
-    if (t == 0) masks[b][0] = masks[b][1] = 0u;
+    const uint32_t *tab = tile_table(sp, tile);
+    swap_tile<C, 0, FORCE, FIXED>(p, sp, Sbuf, stage[b], R, tab + 2, org, __ldg(tab), __ldg(tab + 1), m, jsum);
     __syncthreads();
   }
   if (RED) block_reduce_store(m, jsum, p.partials);
