@@ -444,28 +444,28 @@ struct DirectNode {
   bool fast;      // no wall face and no solid mask: every neighbour is fluid
 
   __device__ __forceinline__ bool setup(const Grid &g) {
-    if (grid_solid(g, x, y, z)) return false;
-    s = (int)grid_slot(g, x, y, z);
-    cell = x + g.nx * (y + g.ny * z);
-    wall = 0;
-    dx[0] = -1;
-    dx[1] = 1;
-    dy[0] = -1;
-    dy[1] = 1;
-    dz[0] = -1;
-    dz[1] = 1;
-    if (x == 0) { if (g.px) dx[0] = g.nx - 1; else wall |= 1u; }
-    if (x == g.nx - 1) { if (g.px) dx[1] = 1 - g.nx; else wall |= 2u; }
-    if (y == 0) { if (g.py) dy[0] = g.ny - 1; else wall |= 4u; }
-    if (y == g.ny - 1) { if (g.py) dy[1] = 1 - g.ny; else wall |= 8u; }
-    if (z == 0) { if (g.pz) dz[0] = g.nz - 1; else wall |= 16u; }
-    if (z == g.nz - 1) { if (g.pz) dz[1] = 1 - g.nz; else wall |= 32u; }
-    dzc[0] = dz[0];
-    dzc[1] = dz[1];
-    if (g.zghost) {
-      dz[0] = -1;
-      dz[1] = 1;
+    // the cell index is needed only for solid lookups (a mask exists)
+    cell = 0;
+    if (g.solid != nullptr) {
+      cell = x + g.nx * (y + g.ny * z);
+      if (g.solid[cell]) return false;
     }
+    // storage slots fit in 31 bits (checked when the geometry is built)
+    s = (x + g.hx) + (int)g.sx * (y + g.hy) + (int)g.sxy * (z + g.hz + (int)g.zoff);
+    const bool xl = x == 0, xh = x == g.nx - 1, yl = y == 0, yh = y == g.ny - 1, zl = z == 0, zh = z == g.nz - 1;
+    // deltas to the -1 / +1 neighbour: wrapped across a periodic face, plain
+    // +-1 at a wall face (the halo slot beyond it; the face also sets its
+    // wall bit)
+    dx[0] = (xl && g.px) ? g.nx - 1 : -1;
+    dx[1] = (xh && g.px) ? 1 - g.nx : 1;
+    dy[0] = (yl && g.py) ? g.ny - 1 : -1;
+    dy[1] = (yh && g.py) ? 1 - g.ny : 1;
+    dzc[0] = (zl && g.pz) ? g.nz - 1 : -1;
+    dzc[1] = (zh && g.pz) ? 1 - g.nz : 1;
+    dz[0] = g.zghost ? -1 : dzc[0];
+    dz[1] = g.zghost ? 1 : dzc[1];
+    wall = (g.px ? 0u : ((unsigned)xl | (unsigned)xh << 1)) | (g.py ? 0u : ((unsigned)yl << 2 | (unsigned)yh << 3)) |
+           (g.pz ? 0u : ((unsigned)zl << 4 | (unsigned)zh << 5));
     fast = wall == 0 && g.solid == nullptr;
     return true;
   }
