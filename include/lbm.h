@@ -226,7 +226,8 @@ typedef struct lbm_batch_config {
   int32_t nodes_per_thread;  /* 1, 2, 4 or 8; block_size * nodes_per_thread divides 4096; 0 = 1 */
   int64_t capacity_slots;    /* node slots of the shared arrays (rounded up to 4096) */
   int32_t max_geometries;    /* size of the geometry table */
-  int32_t reserved;
+  int32_t keep_idx;          /* LBM_AA: 1 = IDX keeps -1 for solid links; 0 = bounce-back slots
+                                folded into IDX when the capacity is below 2^30 (faster) */
   double f16_scale;          /* LBM_F16S: the power-of-two scale of every geometry */
   void *stream;              /* cudaStream_t; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator, as in lbm_config */

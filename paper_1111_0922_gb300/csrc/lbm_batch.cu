@@ -49,6 +49,7 @@ struct BatchParams {
   int t;               // step within the round
   float scale, inv_scale;
   double *partials;    // 2 per work chunk
+  int folded;          // AA: IDX holds bounce-back slots instead of -1 (capacity < 2^30)
 };
 
 template <class C>
@@ -86,6 +87,17 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) 
       const int s2 = launder(s);
 #pragma unroll
       for (int i = 0; i < Q; ++i) A.st(OPP(i), s2, d[i]);
+    } else if (p.folded) {
+      // every IDX entry is a slot: a solid link holds the slot its
+      // bounce-back uses (see k_batch_rebase)
+      d[0] = A.ld(0, s);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) d[i] = A.ld(OPP(i), __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.npad + s));
+      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
+      const int s2 = launder(s);
+      A.st(0, s2, d[0]);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) A.st(i, __ldg(p.idx + (int64_t)(i - 1) * p.npad + s2), d[i]);
     } else {
       d[0] = A.ld(0, s);
 #pragma unroll
@@ -181,8 +193,11 @@ __global__ void k_batch_slot_sums(const BatchSlot *slots, int nslots, const doub
 
 // Copy a geometry's IDX (18 x ipad, node numbers or -1) or packed ET index
 // (9 x ipad) into the batch arrays at `start`, rebased to absolute slots.
+// folded (AA, capacity < 2^30): a solid link k of slot s becomes
+// s + (opp(k) - k) npad, the slot the odd step's bounce-back reads and writes
+// through IDX[k] (as for a single lattice, see k_fold_idx).
 __global__ void k_batch_rebase(const int32_t *src, int64_t ipad, int rows, int64_t n, int32_t *dst, int64_t npad,
-                               int64_t start, int packed) {
+                               int64_t start, int packed, int folded) {
   const int64_t total = (int64_t)rows * n;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / n);
@@ -191,8 +206,12 @@ __global__ void k_batch_rebase(const int32_t *src, int64_t ipad, int rows, int64
     int32_t o;
     if (packed)
       o = (int32_t)(((uint32_t)v & 0x80000000u) | (uint32_t)(((uint32_t)v & 0x7fffffffu) + (uint32_t)start));
+    else if (v >= 0)
+      o = (int32_t)(v + start);
+    else if (folded)
+      o = (int32_t)(start + k + (int64_t)(OPP(r + 1) - (r + 1)) * npad);
     else
-      o = v >= 0 ? (int32_t)(v + start) : -1;
+      o = -1;
     dst[(int64_t)r * npad + start + k] = o;
   }
 }
@@ -259,6 +278,7 @@ struct lbm_batch {
   cudaStream_t stream = nullptr;
   std::string err;
   int64_t capacity = 0;  // slots per array (multiple of kAlign)
+  bool folded = false;   // AA: bounce-back slots folded into IDX
   void *d_A = nullptr;
   int32_t *d_idx = nullptr;
   size_t state_bytes = 0, idx_bytes = 0;
@@ -353,6 +373,7 @@ lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out) {
   b->cfg = *cfg;
   b->stream = static_cast<cudaStream_t>(cfg->stream);
   b->capacity = (cfg->capacity_slots + kAlign - 1) / kAlign * kAlign;
+  b->folded = cfg->variant == LBM_AA && cfg->keep_idx == 0 && b->capacity < ((int64_t)1 << 30);
   b->scale = cfg->precision == LBM_F16S ? (float)cfg->f16_scale : 1.0f;
   b->block_size = cfg->block_size > 0 ? cfg->block_size : 256;
   b->npt = cfg->nodes_per_thread > 0 ? cfg->nodes_per_thread : 1;
@@ -471,6 +492,7 @@ static BatchParams batch_params(const lbm_batch_t *b) {
   p.scale = b->scale;
   p.inv_scale = 1.0f / b->scale;
   p.partials = b->d_partials;
+  p.folded = b->folded ? 1 : 0;
   return p;
 }
 
@@ -564,7 +586,7 @@ lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const in
   }
   if (N > 0)
     k_batch_rebase<<<(unsigned)std::min<int64_t>((rows * N + 255) / 256, 1 << 20), 256, 0, b->stream>>>(
-        src_idx, ipad, rows, N, b->d_idx, b->capacity, start, b->cfg.variant == LBM_ET);
+        src_idx, ipad, rows, N, b->d_idx, b->capacity, start, b->cfg.variant == LBM_ET, b->folded ? 1 : 0);
   // rest state: every deviation zero, the segment's ghosts included
   const size_t es = pdf_bytes(b->cfg.precision);
   for (int i = 0; i < Q; ++i)

@@ -63,7 +63,7 @@ class lbm_batch_config(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("capacity_slots", ctypes.c_int64), ("max_geometries", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("f16_scale", ctypes.c_double),
+                ("keep_idx", ctypes.c_int32), ("f16_scale", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -503,7 +503,7 @@ class Batch:
     """Many sphere-pack geometries on one GPU, advanced together in rounds."""
 
     def __init__(self, capacity_slots, variant="aa", precision="f32", max_geometries=1024,
-                 f16_scale=0.0, block_size=0, nodes_per_thread=0, stream=None,
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, keep_idx=0, stream=None,
                  use_torch_allocator=True):
         cfg = lbm_batch_config()
         cfg.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -513,6 +513,7 @@ class Batch:
         cfg.capacity_slots = int(capacity_slots)
         cfg.max_geometries = int(max_geometries)
         cfg.f16_scale = float(f16_scale)
+        cfg.keep_idx = int(keep_idx)
         self._alloc = None
         if stream is None or use_torch_allocator:
             import torch

@@ -125,3 +125,24 @@ def test_tuner_picks_a_valid_shape(L):
     assert (b.info.block_size, b.info.nodes_per_thread) == (bs, npt)
     b.round(2)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
+def test_folded_and_plain_idx_agree(L, precision):
+    """The AA pattern's batch IDX with bounce-back slots folded in (the
+    default below 2^30 slots) and with -1 kept for solid links give the same
+    bits."""
+    outs = []
+    for keep in (0, 1):
+        b = L.Batch(3 * 16384, variant="aa", precision=precision, max_geometries=8, keep_idx=keep,
+                    f16_scale=2.0 ** 20 if precision == "f16s" else 0.0)
+        slots = [b.admit(p, om, g) for p, om, g in _packs()]
+        b.round(5)
+        b.round(3)
+        outs.append([b.pdfs(s) for s in slots] + [b.poll(s) for s in slots])
+        b.close()
+    for a, c in zip(outs[0], outs[1]):
+        if isinstance(a, np.ndarray):
+            assert np.array_equal(a, c)
+        else:
+            assert a == c
