@@ -14,7 +14,11 @@
 // Inside a CTA every node collides into shared memory; links inside the tile
 // are completed there; a link to a tile of an earlier colour is completed by
 // exchanging with global memory (that tile left its end reversed); a link to a
-// tile of a later colour is left reversed for that tile to complete.
+// tile of a later colour is left reversed for that tile to complete.  Which
+// neighbour tiles are earlier, and from that the class of every link of
+// every cell, comes from per-tile tables built on the host for the geometry
+// (lbm_swap.cu); the reversed slots of earlier tiles are fetched with
+// asynchronous copies while the tile collides.
 //
 // Kernels and launch templates; lbm_swap_f64.cu / _f32.cu / _f16s.cu
 // instantiate them per storage precision, lbm_swap.cu holds the host side.
@@ -49,12 +53,6 @@ __device__ __forceinline__ const uint32_t *tile_table(const SwapPass &sp, const 
 
 // full tile box (cells): 32 along x (one warp per row), 4 along y, 2 along z
 constexpr int kSwapTX = 32, kSwapTY = 4, kSwapTZ = 2;
-
-__device__ __forceinline__ int axis_colour(int t, int nt, int periodic) {
-  if (nt == 1) return 0;
-  if (periodic && (nt & 1)) return t == nt - 1 ? 2 : (t & 1);
-  return t & 1;
-}
 
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
