@@ -114,8 +114,7 @@ typedef struct lbm_config {
                                 persistent blocks (SoA, row pitch a multiple of 16 bytes);
                                 3 = two passes per step: every tile collides and completes its own
                                 links, then one pass completes the links between tiles;
-                                0 = default: 2 for FP32/FP16 storage where allowed, else 1
-                                (measured fastest on GB300) */
+                                0 = default: 1 (measured fastest on GB300) */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

@@ -291,9 +291,9 @@ static LaunchShape pair_shape_of(const lbm_t *h) {
 
 static SwapTiles swap_tiles(const lbm_t *h) {
   SwapTiles t;
-  t.tx = std::min(32, h->cfg.nx);
-  t.ty = std::min(4, h->cfg.ny);
-  t.tz = std::min(2, h->cfg.nz);
+  t.tx = std::min(kSwapTX, h->cfg.nx);
+  t.ty = std::min(kSwapTY, h->cfg.ny);
+  t.tz = std::min(kSwapTZ, h->cfg.nz);
   t.ntx = (h->cfg.nx + t.tx - 1) / t.tx;
   t.nty = (h->cfg.ny + t.ty - 1) / t.ty;
   t.ntz = (h->cfg.nz + t.tz - 1) / t.tz;
@@ -581,7 +581,7 @@ static lbm_status build_geometry(lbm_t *h) {
   }
   h->swap_tma = false;
   if (c.variant == LBM_SWAP && !ind && c.layout == LBM_SOA &&
-      (c.swap_schedule == 2 || (c.swap_schedule == 0 && c.precision != LBM_F64))) {
+      c.swap_schedule == 2) {
     // tensor copies need 16-byte row pitches and inner box extents
     const SwapTiles t = swap_tiles(h);
     const cuuint64_t es = (cuuint64_t)store_size(c.precision);

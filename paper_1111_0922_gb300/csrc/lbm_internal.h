@@ -63,7 +63,13 @@ void launch_cg_ind_ghost(void *A, int64_t npad, int precision, int aos, int64_t 
                          cudaStream_t s);
 void launch_cg_ind_slab(const StepParams &p, const KernelKey &k, const LaunchShape &L);
 
-// lbm_swap.cu: one colour pass of the blocked swap
+// lbm_swap.cu: one colour pass of the blocked swap.  Full tile box (cells):
+// 64 along x (two warps per row), 2 along y, 2 along z; smaller boxes use
+// their own extent.  Measured against 32 x 4 x 2 (FP32, 256^3): the wider
+// rows give longer contiguous runs per array in each colour pass, and more
+// of the links between tiles cross y and z faces, where a warp exchanges
+// whole rows.  The cell classes of the link tables assume kSwapTZ == 2.
+constexpr int kSwapTX = 64, kSwapTY = 2, kSwapTZ = 2;
 struct SwapTiles {
   int tx, ty, tz;       // tile extent in cells
   int ntx, nty, ntz;    // tiles per axis

@@ -37,7 +37,7 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
   g_wait_selftest = mbar_wait(&bar, 0, limit_ns) ? 1 : 2;
 }
 
-// tiles are at most 32 x 4 x 2 = 256 cells (one thread each)
+// tiles are at most kSwapTX x kSwapTY x kSwapTZ = 256 cells (one thread each)
 // ---------------------------------------------------------------------------
 // Link-class tables of the tiles (see SwapTiles).  A tile's colour is fixed
 // by its per-axis colours; a neighbour at offset o is "earlier" when its
@@ -93,7 +93,7 @@ void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, 
           seen[key] = index;
           tables.push_back(em);
           tables.push_back(sm);
-          // cell classes of a full 32 x 4 x 2 tile: x low/inner/high,
+          // cell classes of a full tile: x low/inner/high,
           // y low/inner/high, z low/high
           for (int c = 0; c < 18; ++c) {
             const int xc = c % 3, yc = (c / 3) % 3, zc = c / 9;

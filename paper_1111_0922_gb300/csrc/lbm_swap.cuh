@@ -51,14 +51,13 @@ __device__ __forceinline__ const uint32_t *tile_table(const SwapPass &sp, const 
   return sp.tables + kSwapTableWords * (int)__ldg(sp.tcls + tl);
 }
 
-// full tile box (cells): 32 along x (one warp per row), 4 along y, 2 along z
-constexpr int kSwapTX = 32, kSwapTY = 4, kSwapTZ = 2;
+static_assert(kSwapTX % 32 == 0 && kSwapTX * kSwapTY * kSwapTZ <= 256, "tile box");
 
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
-// FIXED: the tile box is the full 32 x 4 x 2 (every box of at least that
-// size), so shared-memory offsets are compile-time constants.
+// FIXED: the tile box is the full kSwapTX x kSwapTY x kSwapTZ (every box of
+// at least that size), so shared-memory offsets are compile-time constants.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -153,7 +152,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
   }
   // Full tile whose nodes all have every neighbour (no solid mask, no wall
   // face touching the tile): the branch structure below is uniform over each
-  // warp (one warp = one row of 32 cells), the x faces are fixed up after.
+  // warp (a warp covers 32 cells of one row) except on the x faces.
   bool tile_fast = FIXED && g.solid == nullptr && ex == TX && ey == TY && ez == TZ;
   if (FIXED) {
     tile_fast = tile_fast && (g.px || (org[0] > 0 && org[0] + TX < g.nx)) &&
@@ -272,9 +271,16 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
   }
 }
 
-// One pass: the tiles of one colour, one block per tile.
+// One pass: the tiles of one colour, one block per tile.  Full tiles with
+// 4-byte arithmetic fit four blocks per SM (64 registers; measured faster
+// than three, the only spill is a few bytes).
+template <class C, bool FIXED>
+constexpr int swap_min_blocks() {
+  return (FIXED && sizeof(typename C::T) == 4) ? 4 : C::kMinBlocks;
+}
+
 template <class C, int AOS, bool FORCE, bool RED, bool FIXED>
-__global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_pass(StepParams p, SwapPass sp) {
+__global__ void __launch_bounds__(256, (swap_min_blocks<C, FIXED>())) k_swap_pass(StepParams p, SwapPass sp) {
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);

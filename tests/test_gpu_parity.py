@@ -248,7 +248,7 @@ def test_init_density_noise_256_sampled(lbm, variant, precision):
 
 
 @pytest.mark.parametrize("per", [(1, 1, 1), (0, 0, 0), (1, 0, 1), (0, 1, 0)])
-@pytest.mark.parametrize("dims", [(70, 9, 13), (33, 5, 7), (64, 8, 8), (2, 3, 2)])
+@pytest.mark.parametrize("dims", [(70, 9, 13), (33, 5, 7), (64, 8, 8), (2, 3, 2), (150, 4, 3)])
 def test_swap_tiling_and_colouring(lbm, dims, per):
     """Blocked swap over tile counts that are odd, even, one per axis, with
     periodic wrap between tiles and inside a single tile."""
