@@ -275,6 +275,24 @@ static bool use_pairs(const lbm_t *h) {
          c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
 }
 
+// AA pattern with FP16 storage in z pairs (Grid::zpair, kernels in
+// lbm_steps.cuh)?  Needs a full grid without solid cells or halos and an
+// even nz; any_solid and the halos must be known.
+static bool use_zpairs(const lbm_t *h) {
+  const lbm_config &c = h->cfg;
+  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S &&
+         c.pair_x == 0 && c.pair_z != 2 && (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 &&
+         h->grid.hy == 0 && h->grid.hz == 0;
+}
+
+// one thread per column (x, y) and pair plane, nodes_per_thread pair planes
+static LaunchShape zpair_shape_of(const lbm_t *h) {
+  LaunchShape L = shape_of(h);
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 2;
+  L.grid.z = (unsigned)std::min<int64_t>((h->cfg.nz / 2 + npt - 1) / npt, 65535);
+  return L;
+}
+
 static LaunchShape pair_shape_of(const lbm_t *h) {
   LaunchShape L;
   const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
@@ -383,6 +401,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->cg_shift < 0 || (cfg->addressing == LBM_DIRECT && cfg->cg_shift == 1))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift: >= 2 planes on a full grid, >= 1 node on a node list");
   if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
+  if (cfg->pair_z < 0 || cfg->pair_z > 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_z must be 0 .. 2");
   if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
   if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint = 1 needs LBM_OS_PUSH or LBM_OS_PULL with LBM_SOA");
@@ -558,6 +577,7 @@ static lbm_status build_geometry(lbm_t *h) {
     g.sxy = g.sx * (c.ny + 2 * g.hy);
     g.zoff = 0;
     g.solid = h->any_solid ? h->d_solid : nullptr;
+    g.zpair = use_zpairs(h) ? 1 : 0;
     h->nn = ncell;
     h->slots = g.sxy * sz;
     if (h->slots >= ((int64_t)1 << 31) - 1) return fail(h, LBM_ERR_INVALID_ARG, "too many storage slots");
@@ -796,6 +816,7 @@ lbm_status lbm_get_info(const lbm_t *h, lbm_info *info) {
   info->f16_scale = h->scale;
   info->reduce_blocks = h->partial_blocks;
   info->tile_staged = h->swap_tma ? 1 : 0;
+  info->pair_z = h->grid.zpair;
   return LBM_OK;
 }
 
@@ -1099,7 +1120,11 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
     }
     case LBM_AA: {
       StepParams p = params_of(h);
-      if (use_pairs(h)) {
+      if (h->grid.zpair) {
+        const LaunchShape L2 = zpair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_AA, 4 + (int)(h->steps & 1), p, k, L2);
+      } else if (use_pairs(h)) {
         const LaunchShape L2 = pair_shape_of(h);
         if (red_blocks) *red_blocks = (int)blocks_of(L2);
         launch_step_kernel(VAR_AA, 2 + (int)(h->steps & 1), p, k, L2);

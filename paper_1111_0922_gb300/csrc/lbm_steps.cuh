@@ -273,6 +273,157 @@ __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
+// AA pattern with FP16 storage on a full grid without solid cells, nodes in
+// z pairs (Grid::zpair): cells z and z + nz/2 of a column share one 4-byte
+// word of every array, so one thread updates both with 4-byte accesses (half
+// the load and store instructions and twice the bytes per access of one
+// node per thread).  The two updates are the per-node ones above, node by
+// node, so the results equal the one-node-per-thread kernels bit for bit.
+// Along z the pair's words are those of the column's neighbour plane, except
+// across the seam between the halves (plane 0 <-> plane nz/2 - 1), where the
+// neighbour word holds the two cells the other way round.
+
+// Node of the z-pair layout for the odd step's general case (a wall face
+// next to either cell of the pair): neighbour slots from coordinates.
+struct ZPairNode {
+  int x, y, z, s;
+  static constexpr bool fast = false;
+  __device__ __forceinline__ void set(const Grid &g, int x_, int y_, int z_) {
+    x = x_;
+    y = y_;
+    z = z_;
+    s = (int)grid_slot(g, x, y, z);
+  }
+  __device__ __forceinline__ void launder_all() { s = launder(s); }
+  template <bool FAST>
+  __device__ __forceinline__ int nbf(const StepParams &p, int i) const {
+    return nb(p, i);
+  }
+  // slot of the neighbour along c_i, or -1 across a wall
+  __device__ __forceinline__ int nb(const StepParams &p, int i) const {
+    int a = x + CX(i), b = y + CY(i), c = z + CZ(i);
+    if (!wrap_axis(a, p.g.nx, p.g.px) || !wrap_axis(b, p.g.ny, p.g.py) || !wrap_axis(c, p.g.nz, p.g.pz)) return -1;
+    return (int)grid_slot(p.g, a, b, c);
+  }
+};
+
+// Collide both cells of a pair word by word: v[i] holds f_i of the lower
+// cell (low half) and of the upper cell (high half), raw storage units.
+template <bool FORCE>
+__device__ __forceinline__ void zp_collide_pair(__half2 (&v)[Q], const StepParams &p, double &m, double &j) {
+  using C = CodecF16S;
+  float d[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) d[i] = C::raw(__low2half(v[i]));
+  run_collision<C, FORCE>(d, p, m, j);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) v[i] = __halves2half2(C::unraw(d[i]), __high2half(v[i]));
+#pragma unroll
+  for (int i = 0; i < Q; ++i) d[i] = C::raw(__high2half(v[i]));
+  run_collision<C, FORCE>(d, p, m, j);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) v[i] = __halves2half2(__low2half(v[i]), C::unraw(d[i]));
+}
+
+// Even step: node-local, the pair's post-collision PDFs go to the opposite
+// slots of its own word.
+template <bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_even_zp(StepParams p) {
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  double m = 0.0, j = 0.0;
+  if (x < g.nx && y < g.ny) {
+    __half2 *A = static_cast<__half2 *>(p.A);
+    const int64_t nw = p.npad >> 1;  // words per array
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      int w = x + (int)g.sx * y + (int)g.sxy * zw;
+      __half2 v[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
+      zp_collide_pair<FORCE>(v, p, m, j);
+      w = launder(w);  // recompute the store addresses instead of holding 19
+#pragma unroll
+      for (int i = 0; i < Q; ++i) A[OPP(i) * nw + w] = v[i];
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+// Odd step: the words at x - c_i (opposite arrays) in, the words at x + c_i
+// out.  A pair with a wall face next to either cell takes the per-node path.
+template <bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd_zp(StepParams p) {
+  using C = CodecF16S;
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  double m = 0.0, j = 0.0;
+  if (x < g.nx && y < g.ny) {
+    __half2 *A = static_cast<__half2 *>(p.A);
+    const int64_t nw = p.npad >> 1;
+    const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
+    // column deltas to the -1 / +1 neighbour, wrapped across periodic faces
+    // (used only when the column has no wall face)
+    const bool col = (g.px || (x > 0 && x < g.nx - 1)) && (g.py || (y > 0 && y < g.ny - 1));
+    const int dxm = x == 0 ? g.nx - 1 : -1, dxp = x == g.nx - 1 ? 1 - g.nx : 1;
+    const int dym = (y == 0 ? g.ny - 1 : -1) * (int)g.sx, dyp = (y == g.ny - 1 ? 1 - g.ny : 1) * (int)g.sx;
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      if (col && (g.pz || (zw > 0 && zw < H - 1))) {
+        const int w = x + (int)g.sx * y + (int)g.sxy * zw;
+        __half2 v[Q];
+        v[0] = A[w];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int ex = CX(i) > 0 ? dxm : (CX(i) < 0 ? dxp : 0);
+          const int ey = CY(i) > 0 ? dym : (CY(i) < 0 ? dyp : 0);
+          // plane of x - c_i; across the seam the halves are exchanged
+          int ez = 0;
+          bool seam = false;
+          if (CZ(i) > 0) {
+            seam = zw == 0;
+            ez = seam ? (H - 1) * (int)g.sxy : -(int)g.sxy;
+          } else if (CZ(i) < 0) {
+            seam = zw == H - 1;
+            ez = seam ? -(H - 1) * (int)g.sxy : (int)g.sxy;
+          }
+          const __half2 t = A[OPP(i) * nw + (w + ex + ey + ez)];
+          v[i] = seam ? __lowhigh2highlow(t) : t;
+        }
+        zp_collide_pair<FORCE>(v, p, m, j);
+        // recompute the column deltas rather than hold them across the collision
+        const int ws = launder(w), xs = launder(x), ys = launder(y);
+        const int sxm = xs == 0 ? g.nx - 1 : -1, sxp = xs == g.nx - 1 ? 1 - g.nx : 1;
+        const int sym = (ys == 0 ? g.ny - 1 : -1) * (int)g.sx, syp = (ys == g.ny - 1 ? 1 - g.ny : 1) * (int)g.sx;
+        A[ws] = v[0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int ex = CX(i) > 0 ? sxp : (CX(i) < 0 ? sxm : 0);
+          const int ey = CY(i) > 0 ? syp : (CY(i) < 0 ? sym : 0);
+          int ez = 0;
+          bool seam = false;
+          if (CZ(i) > 0) {
+            seam = zw == H - 1;
+            ez = seam ? -(H - 1) * (int)g.sxy : (int)g.sxy;
+          } else if (CZ(i) < 0) {
+            seam = zw == 0;
+            ez = seam ? (H - 1) * (int)g.sxy : -(int)g.sxy;
+          }
+          A[i * nw + (ws + ex + ey + ez)] = seam ? __lowhigh2highlow(v[i]) : v[i];
+        }
+      } else {
+        ZPairNode a;
+        a.set(g, x, y, zw);
+        aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, a, L, m, j);
+        ZPairNode b;
+        b.set(g, x, y, zw + H);
+        aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, b, L, m, j);
+      }
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
 // Esoteric-twist helpers on a full grid (unused for node lists).
 __device__ __forceinline__ int et_pos(const DirectNode &nd, const StepParams &p, int i) { return nd.pos(p, i); }
 __device__ __forceinline__ int et_pos(const IndirectNode &nd, const StepParams &, int) { return nd.s; }
@@ -400,10 +551,20 @@ struct LaunchOS {
     go<false>(p, sub & 1, L);
   }
 };
-// sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full grid)
+// sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full
+// grid); 4 even, 5 odd (z pairs, FP16 storage, SoA full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
+    if (sub >= 4) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+        if (sub == 5)
+          k_aa_odd_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+        else
+          k_aa_even_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      }
+      return;
+    }
     if (sub >= 2) {
       if constexpr (AOS == 0 && !IND) {
         if (sub == 3)

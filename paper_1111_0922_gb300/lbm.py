@@ -46,6 +46,7 @@ class lbm_config(ctypes.Structure):
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("cg_shift", ctypes.c_int32), ("pair_x", ctypes.c_int32),
                 ("store_hint", ctypes.c_int32), ("swap_schedule", ctypes.c_int32),
+                ("pair_z", ctypes.c_int32),
                 ("stream", ctypes.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
@@ -56,7 +57,7 @@ class lbm_info(ctypes.Structure):
                 ("index_bytes", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("natural", ctypes.c_int32), ("kernels_per_step", ctypes.c_int32),
                 ("f16_scale", ctypes.c_double), ("reduce_blocks", ctypes.c_int32),
-                ("tile_staged", ctypes.c_int32)]
+                ("tile_staged", ctypes.c_int32), ("pair_z", ctypes.c_int32)]
 
 
 class lbm_batch_config(ctypes.Structure):
@@ -327,7 +328,7 @@ class Lattice:
     def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
                  layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
                  f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0, pair_x=0,
-                 trt_magic=0.0, store_hint=0, swap_schedule=0, stream=None, use_torch_allocator=True):
+                 trt_magic=0.0, store_hint=0, swap_schedule=0, pair_z=0, stream=None, use_torch_allocator=True):
         self.cfg = lbm_config_default()
         c = self.cfg
         c.nx, c.ny, c.nz = (int(d) for d in dims)
@@ -348,6 +349,7 @@ class Lattice:
         c.pair_x = int(pair_x)
         c.store_hint = int(store_hint)
         c.swap_schedule = int(swap_schedule)
+        c.pair_z = int(pair_z)
         self._alloc = None
         if stream is None or use_torch_allocator:
             import torch

@@ -42,7 +42,7 @@ def setup(args):
     common = dict(variant=args.variant, addressing=args.addressing, layout=args.layout,
                   precision=args.precision, block_size=args.block_size,
                   nodes_per_thread=args.nodes_per_thread, pair_x=args.pair_x,
-                  store_hint=args.store_hint, swap_schedule=args.swap_schedule,
+                  store_hint=args.store_hint, swap_schedule=args.swap_schedule, pair_z=args.pair_z,
                   trt_magic=3.0 / 16.0 if args.trt else 0.0)
     if kind == "dense":
         lat = lbm.Lattice(dims, (1, 1, 1), omega=1.7, **common)
@@ -93,6 +93,8 @@ def main(argv=None):
                     help="OS push/pull, SoA: 1 = cache-streaming stores of the second lattice (OS-NT analogue)")
     ap.add_argument("--swap-schedule", type=int, default=0,
                     help="swap, full grid: 0 default, 1 coloured passes, 2 coloured with tensor-copy staging, 3 two passes")
+    ap.add_argument("--pair-z", type=int, default=0,
+                    help="AA, FP16 storage, full grid: 0 default (z pairs where allowed), 2 one node per thread")
     ap.add_argument("--trt", action="store_true", help="two-relaxation-time collision, magic 3/16")
     args = ap.parse_args(argv)
     import torch

@@ -42,9 +42,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes(lib):
     from paper_1111_0922_gb300 import lbm
 
-    # 3+3+4 int32, 6 doubles, 6 int32, 4 pointers
-    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 6 * 4 + 4 * 8
-    assert ctypes.sizeof(lbm.lbm_info) == 6 * 8 + 2 * 4 + 8 + 2 * 4
+    # 3+3+4 int32, 6 doubles, 7 int32 (+4 bytes of padding), 4 pointers
+    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 7 * 4 + 4 + 4 * 8
+    # 6 int64, 2 int32, 1 double, 3 int32 (+4 bytes of padding)
+    assert ctypes.sizeof(lbm.lbm_info) == 6 * 8 + 2 * 4 + 8 + 3 * 4 + 4
 
 
 def test_host_only_calls(lib):
@@ -72,6 +73,10 @@ def test_host_only_calls(lib):
         assert e.value.status == lbm.LBM_ERR_INVALID_ARG
     bad = lbm.lbm_config_default()
     bad.swap_schedule = 4
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_create(bad)
+    bad = lbm.lbm_config_default()
+    bad.pair_z = 3
     with pytest.raises(lbm.LBMError):
         lbm.lbm_create(bad)
     assert lib.lbm_destroy(None) == 0

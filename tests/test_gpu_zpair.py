@@ -1,0 +1,121 @@
+"""AA pattern with FP16 storage in z pairs (cells z and z + nz/2 in one 4-byte
+word, one thread per pair; Sec. 6, Fig. 5 for the update itself).
+
+The per-node arithmetic is that of the one-node-per-thread kernels, so the
+two layouts give the same PDFs bit for bit; the oracle comparison uses the
+FP16 velocity tolerance of test_gpu_parity (2e-3 relative).
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_U16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    from paper_1111_0922_gb300 import build
+    from paper_1111_0922_gb300 import lbm as lbm_mod
+
+    assert torch.cuda.is_available()
+    build.build()
+    lbm_mod.load()
+    return lbm_mod
+
+
+def _run(L, dims, per, f0, steps, pair_z, g=(0.0, 0.0, 0.0), omega=1.3, solid=None):
+    lat = L.Lattice(dims, per, variant="aa", precision="f16s", omega=omega, force=g, pair_z=pair_z)
+    lat.set_geometry(solid)
+    lat.set_pdfs(f0)
+    lat.step(steps)
+    out = lat.pdfs()
+    paired = lat.info.pair_z
+    lat.close()
+    return out, paired
+
+
+CASES = [
+    ((24, 10, 12), (1, 1, 1)),
+    ((24, 10, 12), (1, 0, 1)),
+    ((24, 10, 12), (0, 1, 0)),
+    ((20, 6, 8), (0, 0, 0)),
+    ((33, 7, 10), (1, 1, 0)),
+    ((16, 8, 2), (1, 1, 1)),
+    ((16, 8, 4), (1, 1, 0)),
+    ((130, 3, 6), (1, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("dims,per", CASES)
+def test_pairs_equal_single_nodes_bitwise(L, dims, per, force):
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n + 3 * per[2] + force)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
+    for steps in (2, 6):
+        a, pa = _run(L, dims, per, f0, steps, 0, g)
+        b, pb = _run(L, dims, per, f0, steps, 2, g)
+        assert pa == 1 and pb == 0
+        assert np.array_equal(a, b), (dims, per, steps)
+
+
+@pytest.mark.parametrize("dims,per", [((24, 10, 12), (1, 1, 1)), ((20, 6, 8), (0, 0, 0)), ((16, 8, 4), (1, 0, 0))])
+def test_pairs_match_oracle(L, dims, per):
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (1e-5, 0.0, -2e-5)
+    out, paired = _run(L, dims, per, f0, 8, 0, g)
+    assert paired == 1
+    ref = oracle.run_push(dims, per, None, f0, 8, 1.3, g)
+    _, ug = oracle.macroscopics(out, g)
+    _, uo = oracle.macroscopics(ref, g)
+    assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= TOL_U16
+
+
+def test_pairs_fused_reduction_and_readout(L):
+    """Mass and flux from the fused reduction and the read-out kernel agree
+    with the one-node-per-thread layout (FP64 sums, 1e-12 relative), and a
+    state written and read back is unchanged."""
+    dims, per = (32, 12, 16), (1, 0, 1)
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(7)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    res = []
+    for pz in (0, 2):
+        lat = L.Lattice(dims, per, variant="aa", precision="f16s", omega=1.2, force=(1e-5, 0, 0), pair_z=pz)
+        lat.set_geometry(None)
+        lat.set_pdfs(f0)
+        back = lat.pdfs()
+        m0, j0 = lat.step_flux(4)
+        m1, j1 = lat.flux()
+        res.append((back, m0, j0, m1, j1))
+        lat.close()
+    (ba, *ra), (bb, *rb) = res
+    assert np.array_equal(ba, bb)
+    for x, y in zip(ra, rb):
+        assert abs(x - y) <= 1e-12 * max(abs(x), abs(y), 1e-30)
+
+
+def test_pairs_off_with_solids_or_odd_nz(L):
+    n = 16 * 8 * 6
+    solid = np.zeros(n, np.uint8)
+    solid[5] = 1
+    lat = L.Lattice((16, 8, 6), (1, 1, 1), variant="aa", precision="f16s")
+    lat.set_geometry(solid)
+    assert lat.info.pair_z == 0
+    lat.close()
+    lat = L.Lattice((16, 8, 5), (1, 1, 1), variant="aa", precision="f16s")
+    lat.set_geometry(None)
+    assert lat.info.pair_z == 0
+    lat.close()
+    lat = L.Lattice((16, 8, 6), (1, 1, 1), variant="aa", precision="f32")
+    lat.set_geometry(None)
+    assert lat.info.pair_z == 0
+    lat.close()
