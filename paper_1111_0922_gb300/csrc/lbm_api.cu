@@ -275,14 +275,16 @@ static bool use_pairs(const lbm_t *h) {
          c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
 }
 
-// AA pattern with FP16 storage in z pairs (Grid::zpair, kernels in
-// lbm_steps.cuh)?  Needs a full grid without solid cells or halos and an
-// even nz; any_solid and the halos must be known.
+// FP16 storage in z pairs (Grid::zpair, kernels in lbm_steps.cuh)?  Two-step,
+// one-step and AA pattern on a full grid without solid cells or halos, with
+// an even nz; any_solid and the halos must be known.
 static bool use_zpairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
-  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S &&
-         c.pair_x == 0 && c.pair_z != 2 && (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 &&
-         h->grid.hy == 0 && h->grid.hz == 0;
+  const bool scheme = c.variant == LBM_AA || c.variant == LBM_TS ||
+                      ((c.variant == LBM_OS_PUSH || c.variant == LBM_OS_PULL) && c.store_hint == 0);
+  return scheme && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S && c.pair_x == 0 &&
+         c.pair_z != 2 && (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 &&
+         h->grid.hz == 0;
 }
 
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
@@ -1107,14 +1109,28 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
   switch (v) {
     case LBM_TS: {
       StepParams p = params_of(h);
-      launch_step_kernel(VAR_TS, 0, p, k, L);
-      launch_step_kernel(VAR_TS, 1, p, key_of(h, false), L);
+      if (h->grid.zpair) {
+        const LaunchShape L2 = zpair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_TS, 2, p, k, L2);
+        launch_step_kernel(VAR_TS, 3, p, key_of(h, false), L2);
+      } else {
+        launch_step_kernel(VAR_TS, 0, p, k, L);
+        launch_step_kernel(VAR_TS, 1, p, key_of(h, false), L);
+      }
       break;
     }
     case LBM_OS_PUSH:
     case LBM_OS_PULL: {
       StepParams p = params_of(h);
-      launch_step_kernel(v == LBM_OS_PUSH ? VAR_OS_PUSH : VAR_OS_PULL, h->cfg.store_hint ? 2 : 0, p, k, L);
+      const int var = v == LBM_OS_PUSH ? VAR_OS_PUSH : VAR_OS_PULL;
+      if (h->grid.zpair) {
+        const LaunchShape L2 = zpair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(var, 4, p, k, L2);
+      } else {
+        launch_step_kernel(var, h->cfg.store_hint ? 2 : 0, p, k, L);
+      }
       std::swap(h->d_A, h->d_B);
       break;
     }

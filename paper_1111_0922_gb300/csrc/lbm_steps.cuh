@@ -350,8 +350,44 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_eve
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
-// Odd step: the words at x - c_i (opposite arrays) in, the words at x + c_i
-// out.  A pair with a wall face next to either cell takes the per-node path.
+// Pair planes next to a column without a wall face (two-step and one-step
+// schemes in z pairs): word of the pair at x + SIGN c_i and whether the seam
+// exchanges its halves.
+struct ZPairCol {
+  int dxm, dxp, dym, dyp;  // word deltas to the -1 / +1 column, periodic wrap
+  __device__ __forceinline__ void set(const Grid &g, int x, int y) {
+    dxm = x == 0 ? g.nx - 1 : -1;
+    dxp = x == g.nx - 1 ? 1 - g.nx : 1;
+    dym = (y == 0 ? g.ny - 1 : -1) * (int)g.sx;
+    dyp = (y == g.ny - 1 ? 1 - g.ny : 1) * (int)g.sx;
+  }
+  template <int SIGN>
+  __device__ __forceinline__ int nbw(const Grid &g, int H, int w, int zw, int i, bool &seam) const {
+    const int cx = SIGN * CX(i), cy = SIGN * CY(i), cz = SIGN * CZ(i);
+    const int ex = cx < 0 ? dxm : (cx > 0 ? dxp : 0);
+    const int ey = cy < 0 ? dym : (cy > 0 ? dyp : 0);
+    int ez = 0;
+    seam = false;
+    if (cz < 0) {
+      seam = zw == 0;
+      ez = seam ? (H - 1) * (int)g.sxy : -(int)g.sxy;
+    } else if (cz > 0) {
+      seam = zw == H - 1;
+      ez = seam ? -(H - 1) * (int)g.sxy : (int)g.sxy;
+    }
+    return w + ex + ey + ez;
+  }
+};
+
+// a pair's column and plane have no wall face next to either cell
+__device__ __forceinline__ bool zp_open_column(const Grid &g, int x, int y) {
+  return (g.px || (x > 0 && x < g.nx - 1)) && (g.py || (y > 0 && y < g.ny - 1));
+}
+__device__ __forceinline__ bool zp_open_plane(const Grid &g, int H, int zw) { return g.pz || (zw > 0 && zw < H - 1); }
+
+// AA pattern, odd step in z pairs: the words at x - c_i (opposite arrays)
+// in, the words at x + c_i out.  A pair with a wall face next to either cell
+// takes the per-node path.
 template <bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd_zp(StepParams p) {
   using C = CodecF16S;
@@ -362,62 +398,170 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd
   if (x < g.nx && y < g.ny) {
     __half2 *A = static_cast<__half2 *>(p.A);
     const int64_t nw = p.npad >> 1;
-    const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
-    // column deltas to the -1 / +1 neighbour, wrapped across periodic faces
-    // (used only when the column has no wall face)
-    const bool col = (g.px || (x > 0 && x < g.nx - 1)) && (g.py || (y > 0 && y < g.ny - 1));
-    const int dxm = x == 0 ? g.nx - 1 : -1, dxp = x == g.nx - 1 ? 1 - g.nx : 1;
-    const int dym = (y == 0 ? g.ny - 1 : -1) * (int)g.sx, dyp = (y == g.ny - 1 ? 1 - g.ny : 1) * (int)g.sx;
+    const bool col = zp_open_column(g, x, y);
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
-      if (col && (g.pz || (zw > 0 && zw < H - 1))) {
+      if (col && zp_open_plane(g, H, zw)) {
         const int w = x + (int)g.sx * y + (int)g.sxy * zw;
         __half2 v[Q];
-        v[0] = A[w];
+        {
+          ZPairCol c;
+          c.set(g, x, y);
+          v[0] = A[w];
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const int ex = CX(i) > 0 ? dxm : (CX(i) < 0 ? dxp : 0);
-          const int ey = CY(i) > 0 ? dym : (CY(i) < 0 ? dyp : 0);
-          // plane of x - c_i; across the seam the halves are exchanged
-          int ez = 0;
-          bool seam = false;
-          if (CZ(i) > 0) {
-            seam = zw == 0;
-            ez = seam ? (H - 1) * (int)g.sxy : -(int)g.sxy;
-          } else if (CZ(i) < 0) {
-            seam = zw == H - 1;
-            ez = seam ? -(H - 1) * (int)g.sxy : (int)g.sxy;
+          for (int i = 1; i < Q; ++i) {
+            bool seam;
+            const __half2 t = A[OPP(i) * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            v[i] = seam ? __lowhigh2highlow(t) : t;
           }
-          const __half2 t = A[OPP(i) * nw + (w + ex + ey + ez)];
-          v[i] = seam ? __lowhigh2highlow(t) : t;
         }
         zp_collide_pair<FORCE>(v, p, m, j);
-        // recompute the column deltas rather than hold them across the collision
+        // recompute the addresses rather than hold them across the collision
         const int ws = launder(w), xs = launder(x), ys = launder(y);
-        const int sxm = xs == 0 ? g.nx - 1 : -1, sxp = xs == g.nx - 1 ? 1 - g.nx : 1;
-        const int sym = (ys == 0 ? g.ny - 1 : -1) * (int)g.sx, syp = (ys == g.ny - 1 ? 1 - g.ny : 1) * (int)g.sx;
+        ZPairCol c;
+        c.set(g, xs, ys);
         A[ws] = v[0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-          const int ex = CX(i) > 0 ? sxp : (CX(i) < 0 ? sxm : 0);
-          const int ey = CY(i) > 0 ? syp : (CY(i) < 0 ? sym : 0);
-          int ez = 0;
-          bool seam = false;
-          if (CZ(i) > 0) {
-            seam = zw == H - 1;
-            ez = seam ? -(H - 1) * (int)g.sxy : (int)g.sxy;
-          } else if (CZ(i) < 0) {
-            seam = zw == 0;
-            ez = seam ? (H - 1) * (int)g.sxy : -(int)g.sxy;
-          }
-          A[i * nw + (ws + ex + ey + ez)] = seam ? __lowhigh2highlow(v[i]) : v[i];
+          bool seam;
+          const int d = c.nbw<1>(g, H, ws, zw, i, seam);
+          A[i * nw + d] = seam ? __lowhigh2highlow(v[i]) : v[i];
         }
       } else {
-        ZPairNode a;
-        a.set(g, x, y, zw);
-        aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, a, L, m, j);
-        ZPairNode b;
-        b.set(g, x, y, zw + H);
-        aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, b, L, m, j);
+        const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
+        for (int h = 0; h < 2; ++h) {
+          ZPairNode a;
+          a.set(g, x, y, zw + h * H);
+          aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, a, L, m, j);
+        }
+      }
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+// Two-step, kernel 1 in z pairs: A -> B at the same words.
+template <bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_ts_collide_zp(StepParams p) {
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  double m = 0.0, j = 0.0;
+  if (x < g.nx && y < g.ny) {
+    const __half2 *A = static_cast<const __half2 *>(p.A);
+    __half2 *B = static_cast<__half2 *>(p.B);
+    const int64_t nw = p.npad >> 1;
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      int w = x + (int)g.sx * y + (int)g.sxy * zw;
+      __half2 v[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
+      zp_collide_pair<FORCE>(v, p, m, j);
+      w = launder(w);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) B[i * nw + w] = v[i];
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+// Two-step, kernel 2 in z pairs: A_i(x) = B_i(x - c_i), raw word copies.
+// (C is CodecF16S; a template so that only that instantiation is emitted.)
+template <class C>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks) k_ts_stream_zp(StepParams p) {
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  __half2 *A = static_cast<__half2 *>(p.A);
+  const __half2 *B = static_cast<const __half2 *>(p.B);
+  const int64_t nw = p.npad >> 1;
+  const bool col = zp_open_column(g, x, y);
+  ZPairCol c;
+  c.set(g, x, y);
+  for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+    if (col && zp_open_plane(g, H, zw)) {
+      int w = x + (int)g.sx * y + (int)g.sxy * zw;
+      __half2 v[Q];
+      v[0] = B[w];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        bool seam;
+        const __half2 t = B[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+        v[i] = seam ? __lowhigh2highlow(t) : t;
+      }
+      w = launder(w);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) A[i * nw + w] = v[i];
+    } else {
+      const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
+      ZPairNode a;
+      a.set(g, x, y, zw);
+      ts_stream_node<false, C, 0, ZPairNode>(p, a, LA, LB);
+      ZPairNode b;
+      b.set(g, x, y, zw + H);
+      ts_stream_node<false, C, 0, ZPairNode>(p, b, LA, LB);
+    }
+  }
+}
+
+// One-step push (PUSH) or pull in z pairs.
+template <bool PUSH, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_os_zp(StepParams p) {
+  using C = CodecF16S;
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  double m = 0.0, j = 0.0;
+  if (x < g.nx && y < g.ny) {
+    const __half2 *A = static_cast<const __half2 *>(p.A);
+    __half2 *B = static_cast<__half2 *>(p.B);
+    const int64_t nw = p.npad >> 1;
+    const bool col = zp_open_column(g, x, y);
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      if (col && zp_open_plane(g, H, zw)) {
+        const int w = x + (int)g.sx * y + (int)g.sxy * zw;
+        __half2 v[Q];
+        if (PUSH) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
+        } else {
+          ZPairCol c;
+          c.set(g, x, y);
+          v[0] = A[w];
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            bool seam;
+            const __half2 t = A[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            v[i] = seam ? __lowhigh2highlow(t) : t;
+          }
+        }
+        zp_collide_pair<FORCE>(v, p, m, j);
+        // recompute the addresses rather than hold them across the collision
+        const int ws = launder(w), xs = launder(x), ys = launder(y);
+        if (PUSH) {
+          ZPairCol c;
+          c.set(g, xs, ys);
+          B[ws] = v[0];
+#pragma unroll
+          for (int i = 1; i < Q; ++i) {
+            bool seam;
+            const int d = c.nbw<1>(g, H, ws, zw, i, seam);
+            B[i * nw + d] = seam ? __lowhigh2highlow(v[i]) : v[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) B[i * nw + ws] = v[i];
+        }
+      } else {
+        const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
+        for (int h = 0; h < 2; ++h) {
+          ZPairNode a;
+          a.set(g, x, y, zw + h * H);
+          if (PUSH)
+            os_push_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
+          else
+            os_pull_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
+        }
       }
     }
   }
@@ -524,14 +668,25 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
 
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchTS {
+  // phase 0 collide, 1 stream; 2 collide, 3 stream in z pairs (FP16 storage, SoA full grid)
   static void run(const StepParams &p, int phase, const LaunchShape &L) {
+    if (phase >= 2) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+        if (phase == 2)
+          k_ts_collide_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+        else
+          k_ts_stream_zp<C><<<L.grid, L.block, 0, L.stream>>>(p);
+      }
+      return;
+    }
     if (phase == 0)
       k_ts_collide<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
     else
       k_ts_stream<C, AOS, NodeOf<IND>><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
-// sub: bit 0 = push (else pull), bit 1 = streaming stores (SoA only)
+// sub: bit 0 = push (else pull), bit 1 = streaming stores (SoA only), bit 2
+// = z pairs (FP16 storage, SoA full grid, no streaming stores)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchOS {
   template <bool CS>
@@ -542,6 +697,15 @@ struct LaunchOS {
       k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED, CS><<<L.grid, L.block, 0, L.stream>>>(p);
   }
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
+    if (sub & 4) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+        if (sub & 1)
+          k_os_zp<true, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+        else
+          k_os_zp<false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      }
+      return;
+    }
     if constexpr (AOS == 0) {
       if (sub & 2) {
         go<true>(p, sub & 1, L);
@@ -594,10 +758,10 @@ void launch_step_kernel_t(int variant, int sub, const StepParams &p, const Kerne
       dispatch_layout<LaunchTS, C>(k.aos, k.ind, k.force, k.red, p, sub, L);
       break;
     case VAR_OS_PUSH:
-      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, 1 | (sub & 2), L);
+      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, 1 | (sub & 6), L);
       break;
     case VAR_OS_PULL:
-      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, sub & 2, L);
+      dispatch_layout<LaunchOS, C>(k.aos, k.ind, k.force, k.red, p, sub & 6, L);
       break;
     case VAR_AA:
       dispatch_layout<LaunchAA, C>(k.aos, k.ind, k.force, k.red, p, sub, L);

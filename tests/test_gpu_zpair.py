@@ -1,5 +1,6 @@
-"""AA pattern with FP16 storage in z pairs (cells z and z + nz/2 in one 4-byte
-word, one thread per pair; Sec. 6, Fig. 5 for the update itself).
+"""FP16 storage in z pairs (cells z and z + nz/2 in one 4-byte word, one
+thread per pair) for the AA pattern (Sec. 6, Fig. 5), the two-step (Sec. 2)
+and the one-step push and pull (Sec. 3) schemes.
 
 The per-node arithmetic is that of the one-node-per-thread kernels, so the
 two layouts give the same PDFs bit for bit; the oracle comparison uses the
@@ -28,8 +29,11 @@ def L():
     return lbm_mod
 
 
-def _run(L, dims, per, f0, steps, pair_z, g=(0.0, 0.0, 0.0), omega=1.3, solid=None):
-    lat = L.Lattice(dims, per, variant="aa", precision="f16s", omega=omega, force=g, pair_z=pair_z)
+VARIANTS = ["aa", "ts", "os_push", "os_pull"]
+
+
+def _run(L, dims, per, f0, steps, pair_z, g=(0.0, 0.0, 0.0), omega=1.3, solid=None, variant="aa"):
+    lat = L.Lattice(dims, per, variant=variant, precision="f16s", omega=omega, force=g, pair_z=pair_z)
     lat.set_geometry(solid)
     lat.set_pdfs(f0)
     lat.step(steps)
@@ -51,27 +55,29 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("force", [False, True])
 @pytest.mark.parametrize("dims,per", CASES)
-def test_pairs_equal_single_nodes_bitwise(L, dims, per, force):
+def test_pairs_equal_single_nodes_bitwise(L, dims, per, force, variant):
     n = int(np.prod(dims))
     rng = np.random.default_rng(n + 3 * per[2] + force)
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
     for steps in (2, 6):
-        a, pa = _run(L, dims, per, f0, steps, 0, g)
-        b, pb = _run(L, dims, per, f0, steps, 2, g)
+        a, pa = _run(L, dims, per, f0, steps, 0, g, variant=variant)
+        b, pb = _run(L, dims, per, f0, steps, 2, g, variant=variant)
         assert pa == 1 and pb == 0
         assert np.array_equal(a, b), (dims, per, steps)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dims,per", [((24, 10, 12), (1, 1, 1)), ((20, 6, 8), (0, 0, 0)), ((16, 8, 4), (1, 0, 0))])
-def test_pairs_match_oracle(L, dims, per):
+def test_pairs_match_oracle(L, dims, per, variant):
     n = int(np.prod(dims))
     rng = np.random.default_rng(n)
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     g = (1e-5, 0.0, -2e-5)
-    out, paired = _run(L, dims, per, f0, 8, 0, g)
+    out, paired = _run(L, dims, per, f0, 8, 0, g, variant=variant)
     assert paired == 1
     ref = oracle.run_push(dims, per, None, f0, 8, 1.3, g)
     _, ug = oracle.macroscopics(out, g)
@@ -79,7 +85,8 @@ def test_pairs_match_oracle(L, dims, per):
     assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= TOL_U16
 
 
-def test_pairs_fused_reduction_and_readout(L):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pairs_fused_reduction_and_readout(L, variant):
     """Mass and flux from the fused reduction and the read-out kernel agree
     with the one-node-per-thread layout (FP64 sums, 1e-12 relative), and a
     state written and read back is unchanged."""
@@ -89,7 +96,7 @@ def test_pairs_fused_reduction_and_readout(L):
     f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
     res = []
     for pz in (0, 2):
-        lat = L.Lattice(dims, per, variant="aa", precision="f16s", omega=1.2, force=(1e-5, 0, 0), pair_z=pz)
+        lat = L.Lattice(dims, per, variant=variant, precision="f16s", omega=1.2, force=(1e-5, 0, 0), pair_z=pz)
         lat.set_geometry(None)
         lat.set_pdfs(f0)
         back = lat.pdfs()
@@ -115,7 +122,10 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.set_geometry(None)
     assert lat.info.pair_z == 0
     lat.close()
-    lat = L.Lattice((16, 8, 6), (1, 1, 1), variant="aa", precision="f32")
-    lat.set_geometry(None)
-    assert lat.info.pair_z == 0
-    lat.close()
+    for variant, kw in (("aa", {"precision": "f32"}), ("cg", {}), ("et", {}), ("swap", {}),
+                        ("os_push", {"store_hint": 1})):
+        kw.setdefault("precision", "f16s")
+        lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
+        lat.set_geometry(None)
+        assert lat.info.pair_z == 0, variant
+        lat.close()
