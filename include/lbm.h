@@ -115,8 +115,9 @@ typedef struct lbm_config {
                                 3 = two passes per step: every tile collides and completes its own
                                 links, then one pass completes the links between tiles;
                                 0 = default: 1 (measured fastest on GB300) */
-  int32_t pair_z;            /* LBM_AA, LBM_TS, LBM_OS_PUSH / PULL (store_hint 0); LBM_F16S, full grid
-                                without solid cells, SoA, even nz, pair_x 0: cells z and z + nz/2
+  int32_t pair_z;            /* LBM_AA, LBM_TS, LBM_OS_PUSH / PULL (store_hint 0), LBM_ET (periodic
+                                box); LBM_F16S, full grid without solid cells, SoA, even nz,
+                                pair_x 0: cells z and z + nz/2
                                 share one 4-byte word per array and one thread updates both (4-byte
                                 accesses); 0 = default (on where allowed),
                                 1 = on where allowed, 2 = off (one node per thread).  The stored

@@ -276,12 +276,14 @@ static bool use_pairs(const lbm_t *h) {
 }
 
 // FP16 storage in z pairs (Grid::zpair, kernels in lbm_steps.cuh)?  Two-step,
-// one-step and AA pattern on a full grid without solid cells or halos, with
-// an even nz; any_solid and the halos must be known.
+// one-step and AA pattern on a full grid without solid cells or halos, the
+// esoteric twist on a periodic one, with an even nz; any_solid and the halos
+// must be known.
 static bool use_zpairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
   const bool scheme = c.variant == LBM_AA || c.variant == LBM_TS ||
-                      ((c.variant == LBM_OS_PUSH || c.variant == LBM_OS_PULL) && c.store_hint == 0);
+                      ((c.variant == LBM_OS_PUSH || c.variant == LBM_OS_PULL) && c.store_hint == 0) ||
+                      (c.variant == LBM_ET && c.periodic[0] && c.periodic[1] && c.periodic[2]);
   return scheme && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S && c.pair_x == 0 &&
          c.pair_z != 2 && (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 &&
          h->grid.hz == 0;
@@ -1151,7 +1153,13 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
     }
     case LBM_ET: {
       StepParams p = params_of(h);
-      launch_step_kernel(VAR_ET, 0, p, k, L);
+      if (h->grid.zpair) {
+        const LaunchShape L2 = zpair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_ET, 1, p, k, L2);
+      } else {
+        launch_step_kernel(VAR_ET, 0, p, k, L);
+      }
       int nm[Q];
       for (int i = 0; i < Q; ++i) nm[i] = h->map[OPP(i)];
       memcpy(h->map, nm, sizeof nm);

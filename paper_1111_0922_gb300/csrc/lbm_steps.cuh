@@ -663,6 +663,53 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
+// Esoteric twist in z pairs (FP16 storage, periodic box without solid cells:
+// every neighbour word exists, no halo).  Array map[i] holds the pair's word
+// at x for the rest and odd directions and at x + c_{i-1} for even i; the
+// post-collision PDFs go back to the same words with the arrays of each
+// opposite pair exchanged, as in et_node.
+template <bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_et_zp(StepParams p) {
+  const Grid &g = p.g;
+  const int H = g.nz >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  double m = 0.0, j = 0.0;
+  auto arr = [&](int k) { return static_cast<__half2 *>(p.mapbase[k]); };
+  if (x < g.nx && y < g.ny) {
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      const int w = x + (int)g.sx * y + (int)g.sxy * zw;
+      __half2 v[Q];
+      {
+        ZPairCol c;
+        c.set(g, x, y);
+        v[0] = arr(0)[w];
+#pragma unroll
+        for (int k = 1; k <= 9; ++k) {
+          const int i = 2 * k - 1;
+          v[i] = arr(i)[w];
+          bool seam;
+          const __half2 t = arr(i + 1)[c.nbw<1>(g, H, w, zw, i, seam)];
+          v[i + 1] = seam ? __lowhigh2highlow(t) : t;
+        }
+      }
+      zp_collide_pair<FORCE>(v, p, m, j);
+      const int ws = launder(w), xs = launder(x), ys = launder(y);
+      ZPairCol c;
+      c.set(g, xs, ys);
+      arr(0)[ws] = v[0];
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        const int i = 2 * k - 1;
+        bool seam;
+        const int q = c.nbw<1>(g, H, ws, zw, i, seam);
+        arr(i + 1)[q] = seam ? __lowhigh2highlow(v[i]) : v[i];
+        arr(i)[ws] = v[i + 1];
+      }
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 
@@ -744,9 +791,15 @@ struct LaunchAA {
       k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
+// sub: 0 one node per thread, 1 z pairs (FP16 storage, SoA, periodic full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchET {
-  static void run(const StepParams &p, int, const LaunchShape &L) {
+  static void run(const StepParams &p, int sub, const LaunchShape &L) {
+    if (sub == 1) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND)
+        k_et_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      return;
+    }
     k_et<C, AOS, IND, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
@@ -767,7 +820,7 @@ void launch_step_kernel_t(int variant, int sub, const StepParams &p, const Kerne
       dispatch_layout<LaunchAA, C>(k.aos, k.ind, k.force, k.red, p, sub, L);
       break;
     case VAR_ET:
-      dispatch_layout<LaunchET, C>(k.aos, k.ind, k.force, k.red, p, 0, L);
+      dispatch_layout<LaunchET, C>(k.aos, k.ind, k.force, k.red, p, sub, L);
       break;
     default:
       break;

@@ -1,6 +1,7 @@
 """FP16 storage in z pairs (cells z and z + nz/2 in one 4-byte word, one
-thread per pair) for the AA pattern (Sec. 6, Fig. 5), the two-step (Sec. 2)
-and the one-step push and pull (Sec. 3) schemes.
+thread per pair) for the AA pattern (Sec. 6, Fig. 5), the two-step (Sec. 2),
+the one-step push and pull (Sec. 3) schemes and, on periodic boxes, the
+esoteric twist (Sec. 7).
 
 The per-node arithmetic is that of the one-node-per-thread kernels, so the
 two layouts give the same PDFs bit for bit; the oracle comparison uses the
@@ -70,6 +71,22 @@ def test_pairs_equal_single_nodes_bitwise(L, dims, per, force, variant):
         assert np.array_equal(a, b), (dims, per, steps)
 
 
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("dims", [(24, 10, 12), (16, 8, 2), (130, 3, 6), (8, 4, 6)])
+def test_et_pairs_equal_single_nodes_bitwise(L, dims, force):
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n + force)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
+    for steps in (1, 2, 5):
+        a, pa = _run(L, dims, (1, 1, 1), f0, steps, 0, g, variant="et")
+        b, pb = _run(L, dims, (1, 1, 1), f0, steps, 2, g, variant="et")
+        assert pa == 1 and pb == 0
+        assert np.array_equal(a, b), (dims, steps)
+    _, pw = _run(L, dims, (1, 0, 1), f0, 1, 0, g, variant="et")
+    assert pw == 0  # walls: halo slots, one node per thread
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dims,per", [((24, 10, 12), (1, 1, 1)), ((20, 6, 8), (0, 0, 0)), ((16, 8, 4), (1, 0, 0))])
 def test_pairs_match_oracle(L, dims, per, variant):
@@ -122,8 +139,7 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.set_geometry(None)
     assert lat.info.pair_z == 0
     lat.close()
-    for variant, kw in (("aa", {"precision": "f32"}), ("cg", {}), ("et", {}), ("swap", {}),
-                        ("os_push", {"store_hint": 1})):
+    for variant, kw in (("aa", {"precision": "f32"}), ("cg", {}), ("swap", {}), ("os_push", {"store_hint": 1})):
         kw.setdefault("precision", "f16s")
         lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
         lat.set_geometry(None)
