@@ -279,13 +279,14 @@ def run_cpu_baseline(target_s=10.0):
 
 
 def run_sweep(torch, lbm, args, hbm):
-    """Every scheme x FP64/FP32 x SoA/AoS on the headline workload."""
+    """Every scheme x FP64/FP32 x SoA/AoS, and FP16 storage in SoA, on the
+    headline workload."""
     out = {}
     n = int(np.prod(DIMS))
     rho_dev = torch.from_numpy(inputs.density_noise(DIMS, seed=SEED)).cuda()
     for variant in model.VARIANTS:
-        for precision in ("f64", "f32"):
-            for layout in ("soa", "aos"):
+        for precision in ("f64", "f32", "f16s"):
+            for layout in (("soa",) if precision == "f16s" else ("soa", "aos")):
                 key = "%s/%s/%s" % (variant, precision, layout)
                 try:
                     lat = make_lattice(lbm, variant, precision, layout)
@@ -300,6 +301,8 @@ def run_sweep(torch, lbm, args, hbm):
                                 "frac": round(mflups / roof, 4),
                                 "bytes_per_flup": model.gpu_bytes(variant, False, precision),
                                 "kernels_per_step": lat.info.kernels_per_step}
+                    if precision == "f16s":
+                        out[key]["pair_z"] = int(lat.info.pair_z)
                     lat.close()
                 except lbm.LBMError as e:
                     out[key] = {"unsupported": str(e).split(": ", 1)[-1][:120]}
