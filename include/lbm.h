@@ -119,7 +119,8 @@ typedef struct lbm_config {
                                 box); LBM_F16S, full grid without solid cells, SoA, even nz,
                                 pair_x 0: cells z and z + nz/2
                                 share one 4-byte word per array and one thread updates both (4-byte
-                                accesses); 0 = default (on where allowed),
+                                accesses); LBM_CG pairs cells y and y + ny/2 instead (even ny);
+                                0 = default (on where allowed),
                                 1 = on where allowed, 2 = off (one node per thread).  The stored
                                 layout is internal: lbm_get_pdfs and friends use natural order. */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
@@ -140,7 +141,7 @@ typedef struct lbm_info {
   double f16_scale;          /* scale in use (LBM_F16S) */
   int32_t reduce_blocks;     /* blocks of the fused reduction */
   int32_t tile_staged;       /* 1 if the swap passes stage tiles with tensor copies */
-  int32_t pair_z;            /* 1 if the AA pattern keeps FP16 cells in z pairs (see lbm_config) */
+  int32_t pair_z;            /* 1 if FP16 cells are stored in pairs (see lbm_config.pair_z) */
 } lbm_info;
 
 typedef struct lbm lbm_t;

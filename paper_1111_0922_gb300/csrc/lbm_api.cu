@@ -289,6 +289,14 @@ static bool use_zpairs(const lbm_t *h) {
          h->grid.hz == 0;
 }
 
+// Compressed grid with FP16 storage in y pairs (Grid::ypair, lbm_cg.cu)?
+// Full grid without solid cells, no x or y halo, even ny.
+static bool use_ypairs(const lbm_t *h) {
+  const lbm_config &c = h->cfg;
+  return c.variant == LBM_CG && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S &&
+         c.pair_z != 2 && (c.ny % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0;
+}
+
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
 static LaunchShape zpair_shape_of(const lbm_t *h) {
   LaunchShape L = shape_of(h);
@@ -582,6 +590,7 @@ static lbm_status build_geometry(lbm_t *h) {
     g.zoff = 0;
     g.solid = h->any_solid ? h->d_solid : nullptr;
     g.zpair = use_zpairs(h) ? 1 : 0;
+    g.ypair = use_ypairs(h) ? 1 : 0;
     h->nn = ncell;
     h->slots = g.sxy * sz;
     if (h->slots >= ((int64_t)1 << 31) - 1) return fail(h, LBM_ERR_INVALID_ARG, "too many storage slots");
@@ -820,7 +829,7 @@ lbm_status lbm_get_info(const lbm_t *h, lbm_info *info) {
   info->f16_scale = h->scale;
   info->reduce_blocks = h->partial_blocks;
   info->tile_staged = h->swap_tma ? 1 : 0;
-  info->pair_z = h->grid.zpair;
+  info->pair_z = (h->grid.zpair || h->grid.ypair) ? 1 : 0;
   return LBM_OK;
 }
 
@@ -1058,6 +1067,7 @@ static lbm_status cg_step(lbm_t *h, bool red, int *red_blocks) {
     LaunchShape L = shape_of(h);  // its grid z covers nz with the planes per thread; refit to the slab
     const int npt = (h->cfg.nz + (int)L.grid.z - 1) / std::max(1, (int)L.grid.z);
     L.grid.z = (unsigned)std::min<int64_t>((z1 - z0 + npt - 1) / npt, 65535);
+    if (h->grid.ypair) L.grid.y = (unsigned)((h->cfg.ny / 2 + (int)L.block.y - 1) / (int)L.block.y);  // word rows
     p.partials = h->d_partials + 2 * used;
     launch_step_kernel_cg(p, k, L);
     used += (int)blocks_of(L);

@@ -17,6 +17,7 @@
 
 #include "lbm_dispatch.cuh"
 #include "lbm_internal.h"
+#include "lbm_steps.cuh"  // zp_collide_pair
 
 namespace lbmk {
 
@@ -29,8 +30,8 @@ constexpr int step_min_cg() {
 
 // One node of a slab: gather at the old offset (the grid's zoff), collide,
 // store at the new offset.  FAST: no wall or solid link.
-template <bool FAST, class C, int AOS, bool FORCE>
-__device__ __forceinline__ void cg_node(const StepParams &p, DirectNode &nd, const Lattice<C, AOS> &A,
+template <bool FAST, class C, int AOS, bool FORCE, class Node>
+__device__ __forceinline__ void cg_node(const StepParams &p, Node &nd, const Lattice<C, AOS> &A,
                                         int64_t shift, double &m, double &j) {
   using T = typename C::T;
   T d[Q];
@@ -90,12 +91,106 @@ __global__ void k_cg_ghost(S *A, int64_t npad, Grid g, int zo) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP16 storage in y pairs (Grid::ypair): cells y and y + ny/2 of a row share
+// one 4-byte word of every array (low and high half), so one thread updates
+// both with 4-byte accesses; z pairs would not survive the plane shifts.
+// Across the seam between the halves (word row 0 against word row ny/2 - 1)
+// the neighbour word holds the two cells the other way round.  The per-node
+// arithmetic is that of cg_node, so the PDFs equal the unpaired ones bit for
+// bit.
+
+// Node of the y-pair layout for the general case (a wall face next to either
+// cell): slots from coordinates at the read offset; along a periodic z axis
+// the ghost planes stand in for the wrapped neighbours, as in DirectNode.
+struct YPairNode {
+  int x, y, z, s;
+  static constexpr bool fast = false;
+  __device__ __forceinline__ void set(const Grid &g, int x_, int y_, int z_) {
+    x = x_;
+    y = y_;
+    z = z_;
+    s = (int)grid_slot(g, x, y, z);
+  }
+  __device__ __forceinline__ void launder_all() { s = launder(s); }
+  template <bool FAST>
+  __device__ __forceinline__ int nbf(const StepParams &p, int i) const {
+    return nb(p, i);
+  }
+  __device__ __forceinline__ int nb(const StepParams &p, int i) const {
+    const Grid &g = p.g;
+    int a = x + CX(i), b = y + CY(i), c = z + CZ(i);
+    if (!wrap_axis(a, g.nx, g.px) || !wrap_axis(b, g.ny, g.py)) return -1;
+    if (!g.pz && (c < 0 || c >= g.nz)) return -1;
+    return (int)grid_slot(g, a, b, c);
+  }
+};
+
+template <bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, CodecF16S::kMinBlocks) k_cg_slab_yp(StepParams p) {
+  using C = CodecF16S;
+  const Grid &g = p.g;
+  const int H = g.ny >> 1;
+  const int pw = (int)(g.sxy >> 1);  // words per plane
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, yw = blockIdx.y * blockDim.y + threadIdx.y;
+  const int shift_w = pw * (p.zo_write - p.zo_read);
+  double m = 0.0, j = 0.0;
+  if (x < g.nx && yw < H) {
+    __half2 *A = static_cast<__half2 *>(p.A);
+    const int64_t nw = p.npad >> 1;
+    const bool row = (g.px || (x > 0 && x < g.nx - 1)) && (g.py || (yw > 0 && yw < H - 1));
+    const int dxm = x == 0 ? g.nx - 1 : -1, dxp = x == g.nx - 1 ? 1 - g.nx : 1;
+    for (int z = p.z0 + blockIdx.z; z < p.z1; z += gridDim.z) {
+      if (row && (g.pz || (z > 0 && z < g.nz - 1))) {
+        const int w = x + (int)g.sx * yw + pw * (z + g.hz + (int)g.zoff);
+        __half2 v[Q];
+        v[0] = A[w];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          // source cell x - c_i; z neighbours are the adjacent planes (ghost
+          // planes on a periodic axis); along y the seam exchanges halves
+          const int ex = CX(i) > 0 ? dxm : (CX(i) < 0 ? dxp : 0);
+          int ey = 0;
+          bool seam = false;
+          if (CY(i) > 0) {
+            seam = yw == 0;
+            ey = seam ? (H - 1) * (int)g.sx : -(int)g.sx;
+          } else if (CY(i) < 0) {
+            seam = yw == H - 1;
+            ey = seam ? -(H - 1) * (int)g.sx : (int)g.sx;
+          }
+          const __half2 t = A[i * nw + (w + ex + ey - CZ(i) * pw)];
+          v[i] = seam ? __lowhigh2highlow(t) : t;
+        }
+        zp_collide_pair<FORCE>(v, p, m, j);
+        const int ws = launder(w) + shift_w;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) A[i * nw + ws] = v[i];
+      } else {
+        const Lattice<C, 0> L{static_cast<__half *>(p.A), p.npad, p.scale, p.inv_scale};
+        const int64_t shift = g.sxy * (int64_t)(p.zo_write - p.zo_read);
+        for (int h = 0; h < 2; ++h) {
+          YPairNode a;
+          a.set(g, x, yw + h * H, z);
+          cg_node<false, C, 0, FORCE>(p, a, L, shift, m, j);
+        }
+      }
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchCG {
   static void run(const StepParams &p, const LaunchShape &L) {
     StepParams q = p;
     q.g.zoff = p.zo_read;
     q.g.zghost = p.g.pz;
+    if (p.g.ypair) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0)
+        k_cg_slab_yp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
+      return;
+    }
     k_cg_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
   }
 };

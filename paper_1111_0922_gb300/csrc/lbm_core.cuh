@@ -114,15 +114,23 @@ struct Grid {
   const uint8_t *solid;  // per cell, or nullptr when every cell is fluid
   int zghost;            // periodic z through ghost planes (compressed grid):
                          // z deltas stay +-1, only the solid lookup wraps
-  int zpair;             // z pairs (AA pattern, FP16 storage, no halo): cells
-                         // z and z + nz/2 share word (x, y, z mod nz/2),
-                         // low and high half; sx, sxy count words
+  int zpair;             // z pairs (FP16 storage, no halo): cells z and
+                         // z + nz/2 share word (x, y, z mod nz/2), low and
+                         // high half; sx, sxy count words
+  int ypair;             // y pairs (compressed grid, FP16 storage, no x or y
+                         // halo): cells y and y + ny/2 share word
+                         // (x, y mod ny/2, z); sx counts words, a plane is
+                         // sxy / 2 words
 };
 
 __device__ __forceinline__ int64_t grid_slot(const Grid &g, int x, int y, int z) {
   if (g.zpair) {
     const int H = g.nz >> 1, hi = z >= H ? 1 : 0;
     return 2 * ((int64_t)x + g.sx * (int64_t)y + g.sxy * (int64_t)(z - hi * H)) + hi;
+  }
+  if (g.ypair) {
+    const int H = g.ny >> 1, hi = y >= H ? 1 : 0;
+    return 2 * ((int64_t)x + g.sx * (int64_t)(y - hi * H) + (g.sxy >> 1) * ((int64_t)z + g.hz + g.zoff)) + hi;
   }
   return (int64_t)(x + g.hx) + g.sx * (int64_t)(y + g.hy) + g.sxy * ((int64_t)z + g.hz + g.zoff);
 }

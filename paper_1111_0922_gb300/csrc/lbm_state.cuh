@@ -28,7 +28,7 @@ struct NodeSlots {
     } else {
       DirectNode nd;
       fluid = nd.init(p, n);
-      s = fluid ? (p.g.zpair ? (int)grid_slot(p.g, nd.x, nd.y, nd.z) : nd.s) : -1;
+      s = fluid ? ((p.g.zpair || p.g.ypair) ? (int)grid_slot(p.g, nd.x, nd.y, nd.z) : nd.s) : -1;
       x = nd.x;
       y = nd.y;
       z = nd.z;

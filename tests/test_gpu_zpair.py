@@ -1,7 +1,8 @@
 """FP16 storage in z pairs (cells z and z + nz/2 in one 4-byte word, one
 thread per pair) for the AA pattern (Sec. 6, Fig. 5), the two-step (Sec. 2),
 the one-step push and pull (Sec. 3) schemes and, on periodic boxes, the
-esoteric twist (Sec. 7).
+esoteric twist (Sec. 7); the compressed grid (Sec. 4) pairs cells y and
+y + ny/2 instead.
 
 The per-node arithmetic is that of the one-node-per-thread kernels, so the
 two layouts give the same PDFs bit for bit; the oracle comparison uses the
@@ -87,7 +88,33 @@ def test_et_pairs_equal_single_nodes_bitwise(L, dims, force):
     assert pw == 0  # walls: halo slots, one node per thread
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
+CG_CASES = [
+    ((24, 10, 12), (1, 1, 1)),
+    ((24, 10, 12), (1, 0, 1)),
+    ((20, 6, 9), (0, 0, 0)),
+    ((33, 8, 7), (1, 1, 0)),
+    ((16, 2, 6), (1, 1, 1)),
+    ((130, 4, 5), (0, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("dims,per", CG_CASES)
+def test_cg_y_pairs_equal_single_nodes_bitwise(L, dims, per, force):
+    """Compressed grid: cells y and y + ny/2 paired (z pairs would not survive
+    the plane shifts); several shifts per run and both sweep directions."""
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n + force)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
+    for steps in (1, 2, 5):
+        a, pa = _run(L, dims, per, f0, steps, 0, g, variant="cg")
+        b, pb = _run(L, dims, per, f0, steps, 2, g, variant="cg")
+        assert pa == 1 and pb == 0
+        assert np.array_equal(a, b), (dims, per, steps)
+
+
+@pytest.mark.parametrize("variant", VARIANTS + ["cg"])
 @pytest.mark.parametrize("dims,per", [((24, 10, 12), (1, 1, 1)), ((20, 6, 8), (0, 0, 0)), ((16, 8, 4), (1, 0, 0))])
 def test_pairs_match_oracle(L, dims, per, variant):
     n = int(np.prod(dims))
@@ -102,7 +129,7 @@ def test_pairs_match_oracle(L, dims, per, variant):
     assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= TOL_U16
 
 
-@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("variant", VARIANTS + ["cg"])
 def test_pairs_fused_reduction_and_readout(L, variant):
     """Mass and flux from the fused reduction and the read-out kernel agree
     with the one-node-per-thread layout (FP64 sums, 1e-12 relative), and a
@@ -139,7 +166,11 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.set_geometry(None)
     assert lat.info.pair_z == 0
     lat.close()
-    for variant, kw in (("aa", {"precision": "f32"}), ("cg", {}), ("swap", {}), ("os_push", {"store_hint": 1})):
+    lat = L.Lattice((16, 7, 6), (1, 1, 1), variant="cg", precision="f16s")  # odd ny
+    lat.set_geometry(None)
+    assert lat.info.pair_z == 0
+    lat.close()
+    for variant, kw in (("aa", {"precision": "f32"}), ("swap", {}), ("os_push", {"store_hint": 1})):
         kw.setdefault("precision", "f16s")
         lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
         lat.set_geometry(None)
