@@ -273,18 +273,20 @@ __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
-// AA pattern with FP16 storage on a full grid without solid cells, nodes in
-// z pairs (Grid::zpair): cells z and z + nz/2 of a column share one 4-byte
-// word of every array, so one thread updates both with 4-byte accesses (half
-// the load and store instructions and twice the bytes per access of one
-// node per thread).  The two updates are the per-node ones above, node by
-// node, so the results equal the one-node-per-thread kernels bit for bit.
-// Along z the pair's words are those of the column's neighbour plane, except
-// across the seam between the halves (plane 0 <-> plane nz/2 - 1), where the
-// neighbour word holds the two cells the other way round.
+// FP16 storage on a full grid without solid cells, nodes in z pairs
+// (Grid::zpair; AA pattern, two-step, one-step push and pull, and the
+// esoteric twist on a periodic box): cells z and z + nz/2 of a column share
+// one 4-byte word of every array, so one thread updates both with 4-byte
+// accesses (half the load and store instructions and twice the bytes per
+// access of one node per thread).  The two updates are the per-node ones
+// above, node by node, so the results equal the one-node-per-thread kernels
+// bit for bit.  Along z the pair's words are those of the column's
+// neighbour plane, except across the seam between the halves (plane 0 <->
+// plane nz/2 - 1), where the neighbour word holds the two cells the other
+// way round.
 
-// Node of the z-pair layout for the odd step's general case (a wall face
-// next to either cell of the pair): neighbour slots from coordinates.
+// Node of the z-pair layout for the general case (a wall face next to either
+// cell of the pair): neighbour slots from coordinates.
 struct ZPairNode {
   int x, y, z, s;
   static constexpr bool fast = false;
