@@ -170,7 +170,8 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.set_geometry(None)
     assert lat.info.pair_z == 0
     lat.close()
-    for variant, kw in (("aa", {"precision": "f32"}), ("swap", {}), ("os_push", {"store_hint": 1})):
+    for variant, kw in (("aa", {"precision": "f32"}), ("swap", {}), ("os_push", {"store_hint": 1}),
+                        ("aa", {"layout": "aos"}), ("aa", {"addressing": "indirect"}), ("aa", {"pair_z": 2})):
         kw.setdefault("precision", "f16s")
         lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
         lat.set_geometry(None)
