@@ -284,17 +284,18 @@ static bool use_zpairs(const lbm_t *h) {
   const bool scheme = c.variant == LBM_AA || c.variant == LBM_TS ||
                       ((c.variant == LBM_OS_PUSH || c.variant == LBM_OS_PULL) && c.store_hint == 0) ||
                       (c.variant == LBM_ET && c.periodic[0] && c.periodic[1] && c.periodic[2]);
-  return scheme && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S && c.pair_x == 0 &&
-         c.pair_z != 2 && (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 &&
-         h->grid.hz == 0;
+  const bool prec = c.precision == LBM_F16S || c.precision == LBM_F32;
+  return scheme && prec && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 0 && c.pair_z != 2 &&
+         (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 && h->grid.hz == 0;
 }
 
 // Compressed grid with FP16 storage in y pairs (Grid::ypair, lbm_cg.cu)?
 // Full grid without solid cells, no x or y halo, even ny.
 static bool use_ypairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
-  return c.variant == LBM_CG && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.precision == LBM_F16S &&
-         c.pair_z != 2 && (c.ny % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0;
+  return c.variant == LBM_CG && c.addressing == LBM_DIRECT && c.layout == LBM_SOA &&
+         (c.precision == LBM_F16S || c.precision == LBM_F32) && c.pair_z != 2 && (c.ny % 2) == 0 && !h->any_solid &&
+         h->grid.hx == 0 && h->grid.hy == 0;
 }
 
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes

@@ -92,9 +92,10 @@ __global__ void k_cg_ghost(S *A, int64_t npad, Grid g, int zo) {
 }
 
 // ---------------------------------------------------------------------------
-// FP16 storage in y pairs (Grid::ypair): cells y and y + ny/2 of a row share
-// one 4-byte word of every array (low and high half), so one thread updates
-// both with 4-byte accesses; z pairs would not survive the plane shifts.
+// FP16 / FP32 storage in y pairs (Grid::ypair): cells y and y + ny/2 of a
+// row share one 4- or 8-byte word of every array (PairWord), so one thread
+// updates both with one access per word; z pairs would not survive the
+// plane shifts.
 // Across the seam between the halves (word row 0 against word row ny/2 - 1)
 // the neighbour word holds the two cells the other way round.  The per-node
 // arithmetic is that of cg_node, so the PDFs equal the unpaired ones bit for
@@ -126,9 +127,10 @@ struct YPairNode {
   }
 };
 
-template <bool FORCE, bool RED>
-__global__ void __launch_bounds__(256, CodecF16S::kMinBlocks) k_cg_slab_yp(StepParams p) {
-  using C = CodecF16S;
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(256, PairWord<C>::kMinBlocks) k_cg_slab_yp(StepParams p) {
+  using PW = PairWord<C>;
+  using W = typename PW::W;
   const Grid &g = p.g;
   const int H = g.ny >> 1;
   const int pw = (int)(g.sxy >> 1);  // words per plane
@@ -136,14 +138,14 @@ __global__ void __launch_bounds__(256, CodecF16S::kMinBlocks) k_cg_slab_yp(StepP
   const int shift_w = pw * (p.zo_write - p.zo_read);
   double m = 0.0, j = 0.0;
   if (x < g.nx && yw < H) {
-    __half2 *A = static_cast<__half2 *>(p.A);
+    W *A = static_cast<W *>(p.A);
     const int64_t nw = p.npad >> 1;
     const bool row = (g.px || (x > 0 && x < g.nx - 1)) && (g.py || (yw > 0 && yw < H - 1));
     const int dxm = x == 0 ? g.nx - 1 : -1, dxp = x == g.nx - 1 ? 1 - g.nx : 1;
     for (int z = p.z0 + blockIdx.z; z < p.z1; z += gridDim.z) {
       if (row && (g.pz || (z > 0 && z < g.nz - 1))) {
         const int w = x + (int)g.sx * yw + pw * (z + g.hz + (int)g.zoff);
-        __half2 v[Q];
+        W v[Q];
         v[0] = A[w];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
@@ -159,15 +161,15 @@ __global__ void __launch_bounds__(256, CodecF16S::kMinBlocks) k_cg_slab_yp(StepP
             seam = yw == H - 1;
             ey = seam ? -(H - 1) * (int)g.sx : (int)g.sx;
           }
-          const __half2 t = A[i * nw + (w + ex + ey - CZ(i) * pw)];
-          v[i] = seam ? __lowhigh2highlow(t) : t;
+          const W t = A[i * nw + (w + ex + ey - CZ(i) * pw)];
+          v[i] = seam ? PW::swap(t) : t;
         }
-        zp_collide_pair<FORCE>(v, p, m, j);
+        zp_collide_pair<C, FORCE>(v, p, m, j);
         const int ws = launder(w) + shift_w;
 #pragma unroll
         for (int i = 0; i < Q; ++i) A[i * nw + ws] = v[i];
       } else {
-        const Lattice<C, 0> L{static_cast<__half *>(p.A), p.npad, p.scale, p.inv_scale};
+        const Lattice<C, 0> L{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
         const int64_t shift = g.sxy * (int64_t)(p.zo_write - p.zo_read);
         for (int h = 0; h < 2; ++h) {
           YPairNode a;
@@ -187,8 +189,8 @@ struct LaunchCG {
     q.g.zoff = p.zo_read;
     q.g.zghost = p.g.pz;
     if (p.g.ypair) {
-      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0)
-        k_cg_slab_yp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
+      if constexpr (kPairable<C> && AOS == 0)
+        k_cg_slab_yp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
       return;
     }
     k_cg_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);

@@ -309,41 +309,72 @@ struct ZPairNode {
   }
 };
 
-// Collide both cells of a pair word by word: v[i] holds f_i of the lower
-// cell (low half) and of the upper cell (high half), raw storage units.
-template <bool FORCE>
-__device__ __forceinline__ void zp_collide_pair(__half2 (&v)[Q], const StepParams &p, double &m, double &j) {
-  using C = CodecF16S;
+// Word of a cell pair: both cells' storage in one aligned word (FP16: the
+// lower cell in the low half; FP32: in .x).  kMinBlocks: resident 256-thread
+// blocks per SM of the pair kernels (FP32 pairs hold both cells' 38 values,
+// so they get 128 registers; measured faster than 80 with spills).
+template <class C>
+struct PairWord;
+template <>
+struct PairWord<CodecF16S> {
+  using W = __half2;
+  static constexpr int kMinBlocks = 3;
+  __device__ static __forceinline__ float lo(W v) { return CodecF16S::raw(__low2half(v)); }
+  __device__ static __forceinline__ float hi(W v) { return CodecF16S::raw(__high2half(v)); }
+  __device__ static __forceinline__ W with_lo(W v, float a) { return __halves2half2(CodecF16S::unraw(a), __high2half(v)); }
+  __device__ static __forceinline__ W with_hi(W v, float b) { return __halves2half2(__low2half(v), CodecF16S::unraw(b)); }
+  __device__ static __forceinline__ W swap(W v) { return __lowhigh2highlow(v); }
+};
+template <>
+struct PairWord<CodecF32> {
+  using W = float2;
+  static constexpr int kMinBlocks = 2;
+  __device__ static __forceinline__ float lo(W v) { return v.x; }
+  __device__ static __forceinline__ float hi(W v) { return v.y; }
+  __device__ static __forceinline__ W with_lo(W v, float a) { return make_float2(a, v.y); }
+  __device__ static __forceinline__ W with_hi(W v, float b) { return make_float2(v.x, b); }
+  __device__ static __forceinline__ W swap(W v) { return make_float2(v.y, v.x); }
+};
+template <class C>
+constexpr bool kPairable = std::is_same<C, CodecF16S>::value || std::is_same<C, CodecF32>::value;
+
+// Collide both cells of a pair word by word: v[i] holds f_i of the lower and
+// of the upper cell, raw storage units.
+template <class C, bool FORCE>
+__device__ __forceinline__ void zp_collide_pair(typename PairWord<C>::W (&v)[Q], const StepParams &p, double &m,
+                                                double &j) {
+  using PW = PairWord<C>;
   float d[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) d[i] = C::raw(__low2half(v[i]));
+  for (int i = 0; i < Q; ++i) d[i] = PW::lo(v[i]);
   run_collision<C, FORCE>(d, p, m, j);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) v[i] = __halves2half2(C::unraw(d[i]), __high2half(v[i]));
+  for (int i = 0; i < Q; ++i) v[i] = PW::with_lo(v[i], d[i]);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) d[i] = C::raw(__high2half(v[i]));
+  for (int i = 0; i < Q; ++i) d[i] = PW::hi(v[i]);
   run_collision<C, FORCE>(d, p, m, j);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) v[i] = __halves2half2(__low2half(v[i]), C::unraw(d[i]));
+  for (int i = 0; i < Q; ++i) v[i] = PW::with_hi(v[i], d[i]);
 }
 
 // Even step: node-local, the pair's post-collision PDFs go to the opposite
 // slots of its own word.
-template <bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_even_zp(StepParams p) {
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_even_zp(StepParams p) {
+  using W = typename PairWord<C>::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   double m = 0.0, j = 0.0;
   if (x < g.nx && y < g.ny) {
-    __half2 *A = static_cast<__half2 *>(p.A);
+    W *A = static_cast<W *>(p.A);
     const int64_t nw = p.npad >> 1;  // words per array
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
       int w = x + (int)g.sx * y + (int)g.sxy * zw;
-      __half2 v[Q];
+      W v[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
-      zp_collide_pair<FORCE>(v, p, m, j);
+      zp_collide_pair<C, FORCE>(v, p, m, j);
       w = launder(w);  // recompute the store addresses instead of holding 19
 #pragma unroll
       for (int i = 0; i < Q; ++i) A[OPP(i) * nw + w] = v[i];
@@ -390,21 +421,22 @@ __device__ __forceinline__ bool zp_open_plane(const Grid &g, int H, int zw) { re
 // AA pattern, odd step in z pairs: the words at x - c_i (opposite arrays)
 // in, the words at x + c_i out.  A pair with a wall face next to either cell
 // takes the per-node path.
-template <bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd_zp(StepParams p) {
-  using C = CodecF16S;
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_odd_zp(StepParams p) {
+  using PW = PairWord<C>;
+  using W = typename PW::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   double m = 0.0, j = 0.0;
   if (x < g.nx && y < g.ny) {
-    __half2 *A = static_cast<__half2 *>(p.A);
+    W *A = static_cast<W *>(p.A);
     const int64_t nw = p.npad >> 1;
     const bool col = zp_open_column(g, x, y);
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
       if (col && zp_open_plane(g, H, zw)) {
         const int w = x + (int)g.sx * y + (int)g.sxy * zw;
-        __half2 v[Q];
+        W v[Q];
         {
           ZPairCol c;
           c.set(g, x, y);
@@ -412,11 +444,11 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             bool seam;
-            const __half2 t = A[OPP(i) * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
-            v[i] = seam ? __lowhigh2highlow(t) : t;
+            const W t = A[OPP(i) * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            v[i] = seam ? PW::swap(t) : t;
           }
         }
-        zp_collide_pair<FORCE>(v, p, m, j);
+        zp_collide_pair<C, FORCE>(v, p, m, j);
         // recompute the addresses rather than hold them across the collision
         const int ws = launder(w), xs = launder(x), ys = launder(y);
         ZPairCol c;
@@ -426,7 +458,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd
         for (int i = 1; i < Q; ++i) {
           bool seam;
           const int d = c.nbw<1>(g, H, ws, zw, i, seam);
-          A[i * nw + d] = seam ? __lowhigh2highlow(v[i]) : v[i];
+          A[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
         }
       } else {
         const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
@@ -442,22 +474,23 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_aa_odd
 }
 
 // Two-step, kernel 1 in z pairs: A -> B at the same words.
-template <bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_ts_collide_zp(StepParams p) {
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_collide_zp(StepParams p) {
+  using W = typename PairWord<C>::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   double m = 0.0, j = 0.0;
   if (x < g.nx && y < g.ny) {
-    const __half2 *A = static_cast<const __half2 *>(p.A);
-    __half2 *B = static_cast<__half2 *>(p.B);
+    const W *A = static_cast<const W *>(p.A);
+    W *B = static_cast<W *>(p.B);
     const int64_t nw = p.npad >> 1;
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
       int w = x + (int)g.sx * y + (int)g.sxy * zw;
-      __half2 v[Q];
+      W v[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
-      zp_collide_pair<FORCE>(v, p, m, j);
+      zp_collide_pair<C, FORCE>(v, p, m, j);
       w = launder(w);
 #pragma unroll
       for (int i = 0; i < Q; ++i) B[i * nw + w] = v[i];
@@ -467,15 +500,16 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_ts_col
 }
 
 // Two-step, kernel 2 in z pairs: A_i(x) = B_i(x - c_i), raw word copies.
-// (C is CodecF16S; a template so that only that instantiation is emitted.)
 template <class C>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks) k_ts_stream_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_stream_zp(StepParams p) {
+  using PW = PairWord<C>;
+  using W = typename PW::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
-  __half2 *A = static_cast<__half2 *>(p.A);
-  const __half2 *B = static_cast<const __half2 *>(p.B);
+  W *A = static_cast<W *>(p.A);
+  const W *B = static_cast<const W *>(p.B);
   const int64_t nw = p.npad >> 1;
   const bool col = zp_open_column(g, x, y);
   ZPairCol c;
@@ -483,13 +517,13 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks) k_ts_stream_zp(S
   for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
     if (col && zp_open_plane(g, H, zw)) {
       int w = x + (int)g.sx * y + (int)g.sxy * zw;
-      __half2 v[Q];
+      W v[Q];
       v[0] = B[w];
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         bool seam;
-        const __half2 t = B[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
-        v[i] = seam ? __lowhigh2highlow(t) : t;
+        const W t = B[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+        v[i] = seam ? PW::swap(t) : t;
       }
       w = launder(w);
 #pragma unroll
@@ -507,22 +541,23 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, C::kMinBlocks) k_ts_stream_zp(S
 }
 
 // One-step push (PUSH) or pull in z pairs.
-template <bool PUSH, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_os_zp(StepParams p) {
-  using C = CodecF16S;
+template <class C, bool PUSH, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_zp(StepParams p) {
+  using PW = PairWord<C>;
+  using W = typename PW::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   double m = 0.0, j = 0.0;
   if (x < g.nx && y < g.ny) {
-    const __half2 *A = static_cast<const __half2 *>(p.A);
-    __half2 *B = static_cast<__half2 *>(p.B);
+    const W *A = static_cast<const W *>(p.A);
+    W *B = static_cast<W *>(p.B);
     const int64_t nw = p.npad >> 1;
     const bool col = zp_open_column(g, x, y);
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
       if (col && zp_open_plane(g, H, zw)) {
         const int w = x + (int)g.sx * y + (int)g.sxy * zw;
-        __half2 v[Q];
+        W v[Q];
         if (PUSH) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
@@ -533,11 +568,11 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_os_zp(
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             bool seam;
-            const __half2 t = A[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
-            v[i] = seam ? __lowhigh2highlow(t) : t;
+            const W t = A[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            v[i] = seam ? PW::swap(t) : t;
           }
         }
-        zp_collide_pair<FORCE>(v, p, m, j);
+        zp_collide_pair<C, FORCE>(v, p, m, j);
         // recompute the addresses rather than hold them across the collision
         const int ws = launder(w), xs = launder(x), ys = launder(y);
         if (PUSH) {
@@ -548,7 +583,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_os_zp(
           for (int i = 1; i < Q; ++i) {
             bool seam;
             const int d = c.nbw<1>(g, H, ws, zw, i, seam);
-            B[i * nw + d] = seam ? __lowhigh2highlow(v[i]) : v[i];
+            B[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
           }
         } else {
 #pragma unroll
@@ -670,17 +705,19 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
 // at x for the rest and odd directions and at x + c_{i-1} for even i; the
 // post-collision PDFs go back to the same words with the arrays of each
 // opposite pair exchanged, as in et_node.
-template <bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_et_zp(StepParams p) {
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_et_zp(StepParams p) {
+  using PW = PairWord<C>;
+  using W = typename PW::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   double m = 0.0, j = 0.0;
-  auto arr = [&](int k) { return static_cast<__half2 *>(p.mapbase[k]); };
+  auto arr = [&](int k) { return static_cast<W *>(p.mapbase[k]); };
   if (x < g.nx && y < g.ny) {
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
       const int w = x + (int)g.sx * y + (int)g.sxy * zw;
-      __half2 v[Q];
+      W v[Q];
       {
         ZPairCol c;
         c.set(g, x, y);
@@ -690,11 +727,11 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_et_zp(
           const int i = 2 * k - 1;
           v[i] = arr(i)[w];
           bool seam;
-          const __half2 t = arr(i + 1)[c.nbw<1>(g, H, w, zw, i, seam)];
-          v[i + 1] = seam ? __lowhigh2highlow(t) : t;
+          const W t = arr(i + 1)[c.nbw<1>(g, H, w, zw, i, seam)];
+          v[i + 1] = seam ? PW::swap(t) : t;
         }
       }
-      zp_collide_pair<FORCE>(v, p, m, j);
+      zp_collide_pair<C, FORCE>(v, p, m, j);
       const int ws = launder(w), xs = launder(x), ys = launder(y);
       ZPairCol c;
       c.set(g, xs, ys);
@@ -704,7 +741,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, CodecF16S::kMinBlocks) k_et_zp(
         const int i = 2 * k - 1;
         bool seam;
         const int q = c.nbw<1>(g, H, ws, zw, i, seam);
-        arr(i + 1)[q] = seam ? __lowhigh2highlow(v[i]) : v[i];
+        arr(i + 1)[q] = seam ? PW::swap(v[i]) : v[i];
         arr(i)[ws] = v[i + 1];
       }
     }
@@ -720,9 +757,9 @@ struct LaunchTS {
   // phase 0 collide, 1 stream; 2 collide, 3 stream in z pairs (FP16 storage, SoA full grid)
   static void run(const StepParams &p, int phase, const LaunchShape &L) {
     if (phase >= 2) {
-      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+      if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (phase == 2)
-          k_ts_collide_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          k_ts_collide_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
         else
           k_ts_stream_zp<C><<<L.grid, L.block, 0, L.stream>>>(p);
       }
@@ -747,11 +784,11 @@ struct LaunchOS {
   }
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub & 4) {
-      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+      if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (sub & 1)
-          k_os_zp<true, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          k_os_zp<C, true, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
         else
-          k_os_zp<false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          k_os_zp<C, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
       }
       return;
     }
@@ -770,11 +807,11 @@ template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub >= 4) {
-      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND) {
+      if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (sub == 5)
-          k_aa_odd_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          k_aa_odd_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
         else
-          k_aa_even_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          k_aa_even_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
       }
       return;
     }
@@ -798,8 +835,8 @@ template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchET {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub == 1) {
-      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && !IND)
-        k_et_zp<FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      if constexpr (kPairable<C> && AOS == 0 && !IND)
+        k_et_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
       return;
     }
     k_et<C, AOS, IND, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
