@@ -218,7 +218,7 @@ def run_headline(torch, lbm, args, rank, world):
     lat.close()
     del rho_dev
     return {"total_s": t_max, "per_launch_s": per_launch, "nodes": n, "clocks": clocks,
-            "kernels": kernels, "rho_host": rho_host}
+            "kernels": kernels, "rho_host": rho_host, "paired": int(info.pair_z)}
 
 
 def run_e2e(torch, lbm, args, rho_host):
@@ -534,13 +534,15 @@ def main_gb300(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": "aa", "precision": "f32 (f - w stored)",
-                   "layout": "soa", "addressing": "direct", "nodes_per_gpu": n,
+                   "layout": "soa" + (", cells z and z + nz/2 paired in 8-byte words" if head["paired"] else ""),
+                   "addressing": "direct", "nodes_per_gpu": n,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state 1.27 GB > 129 MB L2, no flush needed"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                      "bytes_per_launch": int(bytes_launch), "traffic": traffic,
-                     "kernel": "k_aa_even/k_aa_odd<CodecF32,SoA,direct>"},
+                     "kernel": ("k_aa_even_zp/k_aa_odd_zp<CodecF32>" if head["paired"]
+                                else "k_aa_even/k_aa_odd<CodecF32,SoA,direct>")},
         "gpu_launches": head["kernels"],
         "clocks": head["clocks"],
     }
