@@ -275,15 +275,19 @@ static bool use_pairs(const lbm_t *h) {
          c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
 }
 
-// FP16 storage in z pairs (Grid::zpair, kernels in lbm_steps.cuh)?  Two-step,
-// one-step and AA pattern on a full grid without solid cells or halos, the
-// esoteric twist on a periodic one, with an even nz; any_solid and the halos
-// must be known.
+// FP16 / FP32 storage in z pairs (Grid::zpair, kernels in lbm_steps.cuh and
+// lbm_swap.cuh)?  Two-step, one-step and AA pattern on a full grid without
+// solid cells or halos, the esoteric twist on a periodic one, the coloured
+// swap with a periodic z axis and nz a multiple of 4 (at least two tiles of
+// two pair planes, so that no tile spans the seam), with an even nz;
+// any_solid and the halos must be known.
 static bool use_zpairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
   const bool scheme = c.variant == LBM_AA || c.variant == LBM_TS ||
                       ((c.variant == LBM_OS_PUSH || c.variant == LBM_OS_PULL) && c.store_hint == 0) ||
-                      (c.variant == LBM_ET && c.periodic[0] && c.periodic[1] && c.periodic[2]);
+                      (c.variant == LBM_ET && c.periodic[0] && c.periodic[1] && c.periodic[2]) ||
+                      (c.variant == LBM_SWAP && c.periodic[2] && c.swap_schedule <= 1 && (c.nz % 4) == 0 &&
+                       c.nz >= 8);
   const bool prec = c.precision == LBM_F16S || c.precision == LBM_F32;
   return scheme && prec && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 0 && c.pair_z != 2 &&
          (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 && h->grid.hz == 0;
@@ -320,14 +324,18 @@ static LaunchShape pair_shape_of(const lbm_t *h) {
   return L;
 }
 
+// Swap tiles over the grid (with cell pairs: over the grid of pair words,
+// nz/2 planes).
 static SwapTiles swap_tiles(const lbm_t *h) {
   SwapTiles t;
+  t.pairs = h->grid.zpair;
+  const int nz = t.pairs ? h->cfg.nz / 2 : h->cfg.nz;
   t.tx = std::min(kSwapTX, h->cfg.nx);
   t.ty = std::min(kSwapTY, h->cfg.ny);
-  t.tz = std::min(kSwapTZ, h->cfg.nz);
+  t.tz = std::min(kSwapTZ, nz);
   t.ntx = (h->cfg.nx + t.tx - 1) / t.tx;
   t.nty = (h->cfg.ny + t.ty - 1) / t.ty;
-  t.ntz = (h->cfg.nz + t.tz - 1) / t.tz;
+  t.ntz = (nz + t.tz - 1) / t.tz;
   t.colour = 0;
   t.ncolours = swap_colours(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]);
   t.tcls = h->d_swap_tcls;
@@ -1098,6 +1106,12 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
     launch_swap_two_pass(p, t, k, L.grid, L.block, h->stream);
     if (red_blocks) *red_blocks = t.ntx * t.nty * t.ntz;
     return LBM_OK;
+  }
+  if (t.pairs) {
+    // the swap runs on the grid of pair words: nz/2 planes, npad/2 words
+    p.g.nz = h->cfg.nz / 2;
+    p.g.zpair = 0;
+    p.npad = h->npad / 2;
   }
   int used = 0;
   for (int c = 0; c < t.ncolours; ++c) {

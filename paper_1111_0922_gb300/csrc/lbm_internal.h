@@ -82,6 +82,7 @@ struct SwapTiles {
   // *_all: the same for the two-pass schedule (no tile counts as earlier).
   const uint16_t *tcls = nullptr, *tcls_all = nullptr;
   const uint32_t *tables = nullptr, *tables_all = nullptr;
+  int pairs = 0;  // tiles of the grid of cell-pair words (Grid::zpair)
 };
 constexpr int kSwapTableWords = 2 + 3 * 18;
 void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, std::vector<uint16_t> &tcls,

@@ -17,6 +17,10 @@ extern template void swap_pass_t<CodecF32>(const StepParams &, const SwapPass &,
                                            cudaStream_t);
 extern template void swap_pass_t<CodecF16S>(const StepParams &, const SwapPass &, const KernelKey &, size_t,
                                             cudaStream_t);
+extern template void swap_pass_pair_t<CodecPair<CodecF32>>(const StepParams &, const SwapPass &, const KernelKey &,
+                                                           size_t, cudaStream_t);
+extern template void swap_pass_pair_t<CodecPair<CodecF16S>>(const StepParams &, const SwapPass &, const KernelKey &,
+                                                            size_t, cudaStream_t);
 extern template void swap_faces_t<CodecF64>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
 extern template void swap_faces_t<CodecF32>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
 extern template void swap_faces_t<CodecF16S>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
@@ -126,6 +130,10 @@ void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, 
 // buffer (18 words per cell, the stored element or its 4-byte word)
 size_t swap_smem_bytes(const SwapTiles &t, int precision) {
   const size_t cells = (size_t)t.tx * t.ty * t.tz;
+  if (t.pairs) {  // a float2 per PDF; remote words of 8 (FP32) or 4 (FP16) bytes
+    const size_t word = precision == 2 ? 4 : 8;
+    return ((size_t)Q * cells * 8 + 15) / 16 * 16 + (size_t)(Q - 1) * cells * word;
+  }
   const size_t comp = precision == 0 ? 8 : 4, word = precision == 0 ? 8 : 4;
   return ((size_t)Q * cells * comp + 15) / 16 * 16 + (size_t)(Q - 1) * cells * word;
 }
@@ -204,6 +212,13 @@ void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &
   const SwapPass sp = pass_of(p, t);
   if (sp.count[0] * sp.count[1] * sp.count[2] == 0) return;
   const size_t smem = swap_smem_bytes(t, k.precision);
+  if (t.pairs) {
+    if (k.precision == 1)
+      swap_pass_pair_t<CodecPair<CodecF32>>(p, sp, k, smem, s);
+    else if (k.precision == 2)
+      swap_pass_pair_t<CodecPair<CodecF16S>>(p, sp, k, smem, s);
+    return;
+  }
   if (k.precision == 0)
     swap_pass_t<CodecF64>(p, sp, k, smem, s);
   else if (k.precision == 1)

@@ -53,6 +53,49 @@ __device__ __forceinline__ const uint32_t *tile_table(const SwapPass &sp, const 
 
 static_assert(kSwapTX % 32 == 0 && kSwapTX * kSwapTY * kSwapTZ <= 256, "tile box");
 
+// Cell pairs (Grid::zpair: cells z and z + nz/2 in one word) as one storage
+// element: the swap then runs unchanged on the grid of pair words (nz/2
+// planes, z periodic), two collisions per element.  A link across that
+// grid's z wrap joins the two halves the other way round (the seam), so the
+// word is exchanged with its halves swapped.
+template <class C1>
+struct CodecPair {
+  using Single = C1;
+  using S = typename std::conditional<sizeof(typename C1::S) == 2, __half2, float2>::type;
+  using T = float2;
+  static constexpr int kMinBlocks = 2;
+  static constexpr bool kScaled = C1::kScaled;
+  __device__ static __forceinline__ T raw(S v) {
+    if constexpr (sizeof(typename C1::S) == 2)
+      return __half22float2(v);
+    else
+      return v;
+  }
+  __device__ static __forceinline__ S unraw(T v) {
+    if constexpr (sizeof(typename C1::S) == 2)
+      return __floats2half2_rn(v.x, v.y);
+    else
+      return v;
+  }
+};
+template <class C>
+struct IsPairCodec : std::false_type {};
+template <class C1>
+struct IsPairCodec<CodecPair<C1>> : std::true_type {};
+
+// The pull of slot i from x - c_i crosses the seam (pair codecs; z is the
+// pair plane, g.nz the number of pair planes).
+__device__ __forceinline__ bool swap_seam(const Grid &g, int z, int i) {
+  return (CZ(i) > 0 && z == 0) || (CZ(i) < 0 && z == g.nz - 1);
+}
+template <class C>
+__device__ __forceinline__ typename C::T seam_value(typename C::T v, bool seam) {
+  if constexpr (IsPairCodec<C>::value)
+    return seam ? make_float2(v.y, v.x) : v;
+  else
+    return v;
+}
+
 // Index of a neighbour-tile offset (ox, oy, oz) in {-1, 0, 1}^3.
 __host__ __device__ constexpr int tile_bit(int ox, int oy, int oz) { return (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1)); }
 
@@ -181,10 +224,28 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
 #pragma unroll
       for (int i = 0; i < Q; ++i) d[i] = L.ld(i, nd.s);
     }
-    T drho, rjx;
-    collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
-    m += 1.0 + (double)drho;
-    jsum += (double)rjx;
+    if constexpr (IsPairCodec<C>::value) {
+      using C1 = typename C::Single;
+      float da[Q], db[Q], ra, ja, rb, jb;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        da[i] = d[i].x;
+        db[i] = d[i].y;
+      }
+      collide_stored<C1, FORCE>(da, coll_of<float>(p), p.scale, p.inv_scale, ra, ja);
+      collide_stored<C1, FORCE>(db, coll_of<float>(p), p.scale, p.inv_scale, rb, jb);
+      m += 1.0 + (double)ra;
+      jsum += (double)ja;
+      m += 1.0 + (double)rb;
+      jsum += (double)jb;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = make_float2(da[i], db[i]);
+    } else {
+      T drho, rjx;
+      collide_stored<C, FORCE>(d, coll_of<T>(p), p.scale, p.inv_scale, drho, rjx);
+      m += 1.0 + (double)drho;
+      jsum += (double)rjx;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) S[i * TN + t] = d[i];
   }
@@ -209,13 +270,16 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         a = i * TN + (ox ? (cx > 0 ? TX - 1 : 0) : lx - cx) +
             TX * ((oy ? (cy > 0 ? TY - 1 : 0) : ly - cy) + TY * (oz ? (cz > 0 ? TZ - 1 : 0) : lz - cz));
       v[i] = S[a];
-      if (rmask & b) v[i] = fetch_remote<C>(R[(i - 1) * TN + t], nd.nb_fast(p, OPP(i)));
+      if (rmask & b) v[i] = seam_value<C>(fetch_remote<C>(R[(i - 1) * TN + t], nd.nb_fast(p, OPP(i))),
+                                          IsPairCodec<C>::value && swap_seam(g, nd.z, i));
     }
     nd.launder_all();
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       L.st(i, nd.s, v[i]);
-      if (i > 0 && (rmask & (1u << i))) L.st(OPP(i), nd.nb_fast(p, OPP(i)), S[OPP(i) * TN + t]);
+      if (i > 0 && (rmask & (1u << i)))
+        L.st(OPP(i), nd.nb_fast(p, OPP(i)),
+             seam_value<C>(S[OPP(i) * TN + t], IsPairCodec<C>::value && swap_seam(g, nd.z, i)));
     }
   } else if (active) {
     // Gather every incoming value first (the loads from earlier tiles are
@@ -257,7 +321,7 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
         // earlier tile: its reversed slot holds the PDF for us; ours goes there
         if (nd.fast) src = nd.nb_fast(p, OPP(i));
         remote[i] = src;
-        v[i] = L.ld(OPP(i), src);
+        v[i] = seam_value<C>(L.ld(OPP(i), src), IsPairCodec<C>::value && swap_seam(g, nd.z, i));
       } else {
         v[i] = S[OPP(i) * TN + t];  // a later tile completes the link
       }
@@ -266,7 +330,8 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       L.st(i, nd.s, v[i]);
-      if (i > 0 && remote[i] >= 0) L.st(OPP(i), remote[i], S[OPP(i) * TN + t]);
+      if (i > 0 && remote[i] >= 0)
+        L.st(OPP(i), remote[i], seam_value<C>(S[OPP(i) * TN + t], IsPairCodec<C>::value && swap_seam(g, nd.z, i)));
     }
   }
 }
@@ -485,6 +550,22 @@ void swap_pass_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, si
 template <class C>
 void swap_faces_t(const StepParams &p, const SwapPass &sp, int aos, dim3 grid, dim3 block, cudaStream_t s) {
   dispatch_layout<LaunchSwapFaces, C>(aos, false, false, false, p, sp, grid, block, s);
+}
+// Cell pairs: SoA, full grid only, so only those instantiations.
+template <class C>
+void swap_pass_pair_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, size_t smem, cudaStream_t s) {
+  const dim3 blocks(sp.count[0], sp.count[1], sp.count[2]);
+  if (k.force) {
+    if (k.red)
+      LaunchSwap<C, 0, false, true, true>::run(p, sp, smem, blocks, s);
+    else
+      LaunchSwap<C, 0, false, true, false>::run(p, sp, smem, blocks, s);
+  } else {
+    if (k.red)
+      LaunchSwap<C, 0, false, false, true>::run(p, sp, smem, blocks, s);
+    else
+      LaunchSwap<C, 0, false, false, false>::run(p, sp, smem, blocks, s);
+  }
 }
 template <class C>
 int swap_pass_tma_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, const CUtensorMap *map, int nsm,

@@ -1,8 +1,8 @@
 """FP16 and FP32 storage in z pairs (cells z and z + nz/2 in one 4- or 8-byte
 word, one thread per pair) for the AA pattern (Sec. 6, Fig. 5), the two-step (Sec. 2),
 the one-step push and pull (Sec. 3) schemes and, on periodic boxes, the
-esoteric twist (Sec. 7); the compressed grid (Sec. 4) pairs cells y and
-y + ny/2 instead.
+esoteric twist (Sec. 7) and the coloured swap (Sec. 5); the compressed
+grid (Sec. 4) pairs cells y and y + ny/2 instead.
 
 The per-node arithmetic is that of the one-node-per-thread kernels, so the
 two layouts give the same PDFs bit for bit; the oracle comparison uses the
@@ -117,6 +117,43 @@ def test_cg_y_pairs_equal_single_nodes_bitwise(L, dims, per, force, precision):
         assert np.array_equal(a, b), (dims, per, steps)
 
 
+SWAP_CASES = [
+    ((130, 6, 8), (1, 1, 1)),
+    ((64, 4, 12), (1, 0, 1)),
+    ((70, 8, 16), (0, 1, 1)),
+    ((128, 2, 8), (1, 1, 1)),
+    ((64, 6, 8), (1, 1, 1)),
+    ((40, 5, 8), (0, 0, 1)),
+]
+
+
+@pytest.mark.parametrize("precision", ["f16s", "f32"])
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("dims,per", SWAP_CASES)
+def test_swap_pairs_equal_single_nodes_bitwise(L, dims, per, force, precision):
+    """Coloured swap on the grid of pair words (periodic z, nz a multiple of
+    4): tile counts odd and even, one tile along x or y, walls along x or y,
+    cut tiles; links across the seam exchange the halves."""
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n + force)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
+    for steps in (1, 2, 5):
+        a, pa = _run(L, dims, per, f0, steps, 0, g, variant="swap", precision=precision)
+        b, pb = _run(L, dims, per, f0, steps, 2, g, variant="swap", precision=precision)
+        assert pa == 1 and pb == 0
+        assert np.array_equal(a, b), (dims, per, steps)
+
+
+def test_swap_pairs_only_where_allowed(L):
+    for dims, per, kw in (((64, 4, 6), (1, 1, 1), {}), ((64, 4, 8), (1, 1, 0), {}), ((64, 4, 4), (1, 1, 1), {}),
+                          ((64, 4, 8), (1, 1, 1), {"swap_schedule": 2}), ((64, 4, 8), (1, 1, 1), {"swap_schedule": 3})):
+        lat = L.Lattice(dims, per, variant="swap", precision="f32", **kw)
+        lat.set_geometry(None)
+        assert lat.info.pair_z == 0, (dims, per, kw)
+        lat.close()
+
+
 @pytest.mark.parametrize("precision", ["f16s", "f32"])
 @pytest.mark.parametrize("variant", VARIANTS + ["cg"])
 @pytest.mark.parametrize("dims,per", [((24, 10, 12), (1, 1, 1)), ((20, 6, 8), (0, 0, 0)), ((16, 8, 4), (1, 0, 0))])
@@ -175,7 +212,7 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.set_geometry(None)
     assert lat.info.pair_z == 0
     lat.close()
-    for variant, kw in (("aa", {"precision": "f64"}), ("swap", {}), ("os_push", {"store_hint": 1}),
+    for variant, kw in (("aa", {"precision": "f64"}), ("os_push", {"store_hint": 1}),
                         ("aa", {"layout": "aos"}), ("aa", {"addressing": "indirect"}), ("aa", {"pair_z": 2})):
         kw.setdefault("precision", "f16s")
         lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
