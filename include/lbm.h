@@ -120,6 +120,8 @@ typedef struct lbm_config {
                                 pair_x 0: cells z and z + nz/2
                                 share one 4-byte word per array and one thread updates both (4-byte
                                 accesses); LBM_CG pairs cells y and y + ny/2 instead (even ny);
+                                LBM_SWAP (swap_schedule 0 or 1) pairs z when z is periodic and nz
+                                is a multiple of 4 (at least 8);
                                 0 = default (on where allowed),
                                 1 = on where allowed, 2 = off (one node per thread).  The stored
                                 layout is internal: lbm_get_pdfs and friends use natural order. */
