@@ -293,7 +293,7 @@ static bool use_zpairs(const lbm_t *h) {
          (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 && h->grid.hz == 0;
 }
 
-// Compressed grid with FP16 storage in y pairs (Grid::ypair, lbm_cg.cu)?
+// Compressed grid with FP16 / FP32 storage in y pairs (Grid::ypair, lbm_cg.cu)?
 // Full grid without solid cells, no x or y halo, even ny.
 static bool use_ypairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;

@@ -114,10 +114,10 @@ struct Grid {
   const uint8_t *solid;  // per cell, or nullptr when every cell is fluid
   int zghost;            // periodic z through ghost planes (compressed grid):
                          // z deltas stay +-1, only the solid lookup wraps
-  int zpair;             // z pairs (FP16 storage, no halo): cells z and
-                         // z + nz/2 share word (x, y, z mod nz/2), low and
-                         // high half; sx, sxy count words
-  int ypair;             // y pairs (compressed grid, FP16 storage, no x or y
+  int zpair;             // z pairs (FP16 / FP32 storage, no halo): cells z
+                         // and z + nz/2 share word (x, y, z mod nz/2), low
+                         // and high half; sx, sxy count words
+  int ypair;             // y pairs (compressed grid, FP16 / FP32, no x or y
                          // halo): cells y and y + ny/2 share word
                          // (x, y mod ny/2, z); sx counts words, a plane is
                          // sxy / 2 words

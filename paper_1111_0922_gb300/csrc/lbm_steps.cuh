@@ -273,12 +273,12 @@ __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
-// FP16 storage on a full grid without solid cells, nodes in z pairs
+// FP16 / FP32 storage on a full grid without solid cells, nodes in z pairs
 // (Grid::zpair; AA pattern, two-step, one-step push and pull, and the
 // esoteric twist on a periodic box): cells z and z + nz/2 of a column share
-// one 4-byte word of every array, so one thread updates both with 4-byte
-// accesses (half the load and store instructions and twice the bytes per
-// access of one node per thread).  The two updates are the per-node ones
+// one word of every array (PairWord), so one thread updates both with one
+// access per word (half the load and store instructions and twice the bytes
+// per access of one node per thread).  The two updates are the per-node ones
 // above, node by node, so the results equal the one-node-per-thread kernels
 // bit for bit.  Along z the pair's words are those of the column's
 // neighbour plane, except across the seam between the halves (plane 0 <->
@@ -700,7 +700,7 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
-// Esoteric twist in z pairs (FP16 storage, periodic box without solid cells:
+// Esoteric twist in z pairs (FP16 / FP32 storage, periodic box without solid cells:
 // every neighbour word exists, no halo).  Array map[i] holds the pair's word
 // at x for the rest and odd directions and at x + c_{i-1} for even i; the
 // post-collision PDFs go back to the same words with the arrays of each
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_et_z
 
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchTS {
-  // phase 0 collide, 1 stream; 2 collide, 3 stream in z pairs (FP16 storage, SoA full grid)
+  // phase 0 collide, 1 stream; 2 collide, 3 stream in z pairs (FP16 / FP32, SoA full grid)
   static void run(const StepParams &p, int phase, const LaunchShape &L) {
     if (phase >= 2) {
       if constexpr (kPairable<C> && AOS == 0 && !IND) {
@@ -772,7 +772,7 @@ struct LaunchTS {
   }
 };
 // sub: bit 0 = push (else pull), bit 1 = streaming stores (SoA only), bit 2
-// = z pairs (FP16 storage, SoA full grid, no streaming stores)
+// = z pairs (FP16 / FP32 storage, SoA full grid, no streaming stores)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchOS {
   template <bool CS>
@@ -802,7 +802,7 @@ struct LaunchOS {
   }
 };
 // sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full
-// grid); 4 even, 5 odd (z pairs, FP16 storage, SoA full grid)
+// grid); 4 even, 5 odd (z pairs, FP16 / FP32 storage, SoA full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
@@ -830,7 +830,7 @@ struct LaunchAA {
       k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
   }
 };
-// sub: 0 one node per thread, 1 z pairs (FP16 storage, SoA, periodic full grid)
+// sub: 0 one node per thread, 1 z pairs (FP16 / FP32 storage, SoA, periodic full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchET {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
