@@ -171,7 +171,7 @@ def test_pairs_match_oracle(L, dims, per, variant, precision):
 
 
 @pytest.mark.parametrize("precision", ["f16s", "f32"])
-@pytest.mark.parametrize("variant", VARIANTS + ["cg"])
+@pytest.mark.parametrize("variant", VARIANTS + ["cg", "swap"])
 def test_pairs_fused_reduction_and_readout(L, variant, precision):
     """Mass and flux from the fused reduction and the read-out kernel agree
     with the one-node-per-thread layout (FP64 sums, 1e-12 relative), and a
