@@ -303,9 +303,13 @@ static bool use_ypairs(const lbm_t *h) {
 }
 
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
+// (default 2; 4 for the FP16 AA pattern: 75.1 vs 73.3 GFLUP/s on 256^3,
+// FP32 best at 2)
 static LaunchShape zpair_shape_of(const lbm_t *h) {
   LaunchShape L = shape_of(h);
-  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 2;
+  const int npt = h->cfg.nodes_per_thread > 0
+                      ? h->cfg.nodes_per_thread
+                      : ((h->cfg.variant == LBM_AA && h->cfg.precision == LBM_F16S) ? 4 : 2);
   L.grid.z = (unsigned)std::min<int64_t>((h->cfg.nz / 2 + npt - 1) / npt, 65535);
   return L;
 }
