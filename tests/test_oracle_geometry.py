@@ -2,7 +2,6 @@
 in plain Python on small boxes, the Boolean-model porosity law on a large
 box, and the equality of the sparse (IDX) step with the full-grid step."""
 import itertools
-import math
 
 import numpy as np
 import pytest

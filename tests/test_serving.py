@@ -5,10 +5,9 @@ and that every result equals the same geometry solved alone."""
 import math
 
 import numpy as np
-import pytest
 
 import oracle
-from paper_1111_0922_gb300 import inputs, serving
+from paper_1111_0922_gb300 import serving
 
 
 class OracleEngine:
