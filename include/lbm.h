@@ -115,16 +115,16 @@ typedef struct lbm_config {
                                 3 = two passes per step: every tile collides and completes its own
                                 links, then one pass completes the links between tiles;
                                 0 = default: 1 (measured fastest on GB300) */
-  int32_t pair_z;            /* LBM_AA, LBM_TS, LBM_OS_PUSH / PULL (store_hint 0), LBM_ET (periodic
-                                box); LBM_F16S, full grid without solid cells, SoA, even nz,
-                                pair_x 0: cells z and z + nz/2
-                                share one 4-byte word per array and one thread updates both (4-byte
-                                accesses); LBM_CG pairs cells y and y + ny/2 instead (even ny);
-                                LBM_SWAP (swap_schedule 0 or 1) pairs z when z is periodic and nz
-                                is a multiple of 4 (at least 8);
-                                0 = default (on where allowed),
-                                1 = on where allowed, 2 = off (one node per thread).  The stored
-                                layout is internal: lbm_get_pdfs and friends use natural order. */
+  int32_t pair_z;            /* Cell pairs, LBM_F16S or LBM_F32 storage, SoA, full grid without
+                                solid cells, pair_x 0: LBM_AA, LBM_TS, LBM_OS_PUSH / PULL
+                                (store_hint 0) and LBM_ET (periodic box) keep cells z and z + nz/2
+                                (even nz) in one word per array (4 bytes FP16, 8 bytes FP32), and
+                                one thread updates both; LBM_CG pairs cells y and y + ny/2 instead
+                                (even ny); LBM_SWAP (swap_schedule 0 or 1) pairs z when z is
+                                periodic and nz is a multiple of 4 (at least 8).  0 = default (on
+                                where allowed), 1 = on where allowed, 2 = off (one node per
+                                thread).  The stored layout is internal: lbm_get_pdfs and friends
+                                use natural order. */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */
@@ -143,7 +143,7 @@ typedef struct lbm_info {
   double f16_scale;          /* scale in use (LBM_F16S) */
   int32_t reduce_blocks;     /* blocks of the fused reduction */
   int32_t tile_staged;       /* 1 if the swap passes stage tiles with tensor copies */
-  int32_t pair_z;            /* 1 if FP16 cells are stored in pairs (see lbm_config.pair_z) */
+  int32_t pair_z;            /* 1 if cells are stored in pairs (see lbm_config.pair_z) */
 } lbm_info;
 
 typedef struct lbm lbm_t;
