@@ -2,16 +2,19 @@
 
 Headline workload: a periodic 256^3 full grid (direct addressing), density
 rho = 1 + 1e-3 U[-1, 1) (SplitMix64 seed 2), zero velocity, omega = 1.7,
-AA pattern, FP32 storage of f - w, SoA.  One bench step is one time step of
-the whole lattice (one kernel launch for the AA pattern).  The state (1.27 GB)
-is larger than L2 (129 MB), so no flush is needed between steps.
+AA pattern, SoA, in the paper's arithmetic: FP64 storage of f - w and FP64
+collision.  One bench step is one time step of the whole lattice (one kernel
+launch for the AA pattern).  The state (2.55 GB) is larger than L2 (129 MB),
+so no flush is needed between steps.
 
-Printed (rank 0, one JSON line): MFLUP/s of the headline run, the roofline of
-its kernel against the measured HBM copy bandwidth, an end-to-end figure
-through the C ABI with host buffers, the FP64 CPU oracle timed on the host
-cores, SM clocks sampled during the timed region, and a sweep over every
-propagation scheme x FP64/FP32 x SoA/AoS with each one's fraction of its own
-roofline.
+Printed (rank 0, one JSON line): MFLUP/s of the headline run; the roofline of
+its kernel, bound by the FP64 pipe (peak = SMs x FP64 instructions per SM
+clock x the SM clock sampled during the timed region; instructions per update
+from the committed ncu capture); the same workload with FP32 and FP16 storage
+(each with its HBM roofline); an end-to-end figure through the C ABI with
+host buffers; the FP64 CPU oracle timed on the host cores; SM clocks sampled
+during the timed region; and a sweep over every propagation scheme x
+FP64/FP32/FP16 x SoA/AoS with each one's fraction of its own roofline.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gb300|reference]
 N > 1 runs under torchrun as N independent replicas (weak scaling, no
@@ -56,33 +59,73 @@ def measured_peaks():
     return FALLBACK_HBM, "fallback"
 
 
-HEADLINE_SOURCES = ("lbm_core.cuh", "lbm_dispatch.cuh", "lbm_steps.cuh", "lbm_steps_f32.cu")
+STEP_SOURCES = ("lbm_core.cuh", "lbm_dispatch.cuh", "lbm_steps.cuh")
 
 
-def kernel_source_hash(names=HEADLINE_SOURCES):
-    """Hash of the files that define the headline kernels (k_aa_even/odd,
-    FP32): a profile's DRAM counters stay valid while this does not change."""
+def kernel_source_hash(precision="f32"):
+    """Hash of the files that define the step kernels of one precision
+    (k_aa_even/odd and the other one-lattice schemes): a profile's counters
+    stay valid while this does not change."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1111_0922_gb300", "csrc")
-    for name in names:
+    for name in STEP_SOURCES + ("lbm_steps_%s.cu" % precision,):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_key):
-    """DRAM bytes per launch of a kernel from the committed ncu summary (a
-    line `dram_bytes_per_launch <key> <bytes> source_hash <hash>` in a file of
-    profiles/), or None when the kernel sources changed since the capture."""
+def profile_records():
+    """Machine-readable lines of the committed ncu summaries (profiles/*.md):
+      dram_bytes_per_launch <key> <bytes> source_hash <hash>
+      fp64_inst_per_flup <collision kind> <count> source_hash <hash>
+      fp64_inst_per_clk_sm <peak>
+    returned as lists of fields."""
+    recs = []
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) == 5 and parts[0] == "dram_bytes_per_launch" and parts[1] == kernel_key \
-                        and parts[3] == "source_hash":
-                    return float(parts[2]) if parts[4] == kernel_source_hash() else None
+                if parts and parts[0] in ("dram_bytes_per_launch", "fp64_inst_per_flup", "fp64_inst_per_clk_sm"):
+                    recs.append(parts)
+    return recs
+
+
+def profiled_traffic(kernel_key, precision):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the kernel sources changed since the capture."""
+    for p in profile_records():
+        if len(p) == 5 and p[0] == "dram_bytes_per_launch" and p[1] == kernel_key and p[3] == "source_hash":
+            return float(p[2]) if p[4] == kernel_source_hash(precision) else None
     return None
+
+
+def profiled_fp64():
+    """(FP64 thread instructions per SM clock, {collision kind: FP64 thread
+    instructions per update}) from the committed ncu capture; a count whose
+    kernel sources changed since the capture is left out."""
+    per_clk = None
+    per_flup = {}
+    for p in profile_records():
+        if p[0] == "fp64_inst_per_clk_sm" and len(p) == 2:
+            per_clk = float(p[1])
+        elif p[0] == "fp64_inst_per_flup" and len(p) == 5 and p[4] == kernel_source_hash("f64"):
+            per_flup[p[1]] = float(p[2])
+    return per_clk, per_flup
+
+
+def fp64_pipe(torch, dev, clocks):
+    """The FP64-pipe roof of this GPU from measured inputs (model.Fp64Pipe),
+    or None when the capture is missing or stale."""
+    per_clk, per_flup = profiled_fp64()
+    if per_clk is None or set(per_flup) != set(model.COLLISIONS):
+        return None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if clocks and clocks.get("sm_mhz"):
+        ghz = clocks["sm_mhz"] / 1e3
+    else:
+        return None
+    return model.Fp64Pipe(sms, ghz, per_clk, per_flup)
 
 
 # ---------------------------------------------------------------------------
@@ -191,19 +234,23 @@ def timed_steps(torch, lat, steps, per_launch=True):
     return total, total / steps
 
 
-def run_headline(torch, lbm, args, rank, world):
+def run_headline(torch, lbm, args, rank, world, precision="f64", sample_clocks=True):
+    """The headline workload with the given storage precision (AA pattern,
+    SoA, direct): W warm-up steps, then K steps between CUDA events on the
+    launching stream, a barrier and a synchronize on both sides."""
     dev = torch.cuda.current_device()
     n = int(np.prod(DIMS))
     rho_host = inputs.density_noise(DIMS, seed=SEED)
     rho_dev = torch.from_numpy(rho_host).to(f"cuda:{dev}")
-    lat = make_lattice(lbm, "aa", "f32", "soa")
+    lat = make_lattice(lbm, "aa", precision, "soa")
     lat.set_geometry(None)
     lat.init(rho_dev, on_device=True)
     lat.step(args.warmup if args.warmup % 2 == 0 else args.warmup + 1)
     torch.cuda.synchronize()
-    sampler = ClockSampler(gpu_smi_id(torch, dev))
-    sampler.start()
-    time.sleep(0.3)
+    sampler = ClockSampler(gpu_smi_id(torch, dev)) if sample_clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -211,17 +258,60 @@ def run_headline(torch, lbm, args, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     info = lat.info
     t_max = max_over_ranks(torch, total, f"cuda:{dev}")
     kernels = args.steps * info.kernels_per_step
     lat.close()
     del rho_dev
+    torch.cuda.empty_cache()
     return {"total_s": t_max, "per_launch_s": per_launch, "nodes": n, "clocks": clocks,
-            "kernels": kernels, "rho_host": rho_host, "paired": int(info.pair_z)}
+            "kernels": kernels, "rho_host": rho_host, "paired": int(info.pair_z), "precision": precision}
 
 
-def run_e2e(torch, lbm, args, rho_host):
+def hbm_roofline(head, hbm, peak_kind, steps):
+    """HBM roofline of an FP32 / FP16 headline run (its AA kernels)."""
+    prec = head["precision"]
+    bytes_launch = head["nodes"] * model.kernel_bytes_per_flup("aa", False, prec)
+    achieved = bytes_launch / head["per_launch_s"] / 1e9
+    key = "aa_%s_soa_direct_256" % prec
+    codec = {"f32": "CodecF32", "f16s": "CodecF16S"}[prec]
+    return {"mflups": round(head["nodes"] * steps / head["total_s"] / 1e6, 1),
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "bytes_per_launch": int(bytes_launch),
+            "traffic": profiled_traffic(key, prec),
+            "kernel": ("k_aa_even_zp/k_aa_odd_zp<%s>" % codec if head["paired"]
+                       else "k_aa_even/k_aa_odd<%s,SoA,direct>" % codec)}
+
+
+def fp64_roofline(head, pipe, hbm, peak_kind):
+    """FP64-pipe roofline of the FP64 headline run: achieved = FP64 thread
+    instructions per launch (captured count per update x nodes) / mean
+    CUDA-event launch duration; peak = SMs x FP64 instructions per SM clock
+    x the SM clock sampled during the timed region."""
+    n = head["nodes"]
+    bytes_launch = n * model.kernel_bytes_per_flup("aa", False, "f64")
+    hbm_achieved = bytes_launch / head["per_launch_s"] / 1e9
+    out = {"bound": "alu", "unit": "G FP64 inst/s", "kernel": "k_aa_even/k_aa_odd<CodecF64,SoA,direct>",
+           "bytes_per_launch": int(bytes_launch), "traffic": profiled_traffic("aa_f64_soa_direct_256", "f64"),
+           "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm, "unit": "GB/s",
+                   "frac": round(hbm_achieved / hbm, 4), "peak_kind": peak_kind}}
+    if pipe is None:
+        out.update({"achieved": None, "peak": None, "frac": None,
+                    "peak_kind": "unavailable: FP64 capture missing or stale, or no clock samples"})
+        return out
+    inst = pipe.inst_per_flup["bgk"] * n
+    achieved = inst / head["per_launch_s"] / 1e9
+    peak = pipe.inst_rate() / 1e9
+    out.update({"achieved": round(achieved, 1), "peak": round(peak, 1), "frac": round(achieved / peak, 4),
+                "peak_kind": "measured (SM count: device attribute; SM clock: median sampled in the timed "
+                             "region; FP64 instructions per clock and per update: ncu, profiles/)",
+                "inst_per_launch": int(inst), "fp64_pipe": pipe.as_dict(),
+                "roof_mflups": round(pipe.roof_mflups(), 1)})
+    return out
+
+
+def run_e2e(torch, lbm, args, rho_host, precision="f64"):
     """The same solve through the public API with host buffers: the initial
     density goes up from pinned host memory, the mass/flux come back every 100
     steps through the fused reduction, and the final density field comes back
@@ -229,7 +319,7 @@ def run_e2e(torch, lbm, args, rho_host):
     n = rho_host.size
     pin_rho = torch.from_numpy(rho_host).pin_memory()
     pin_out = torch.empty(n, dtype=torch.float64).pin_memory()
-    lat = make_lattice(lbm, "aa", "f32", "soa")
+    lat = make_lattice(lbm, "aa", precision, "soa")
     lat.set_geometry(None)
     check = 100
     torch.cuda.synchronize()
@@ -253,7 +343,7 @@ def run_e2e(torch, lbm, args, rho_host):
     secs = t1 - t0
     return {"value": n * done / secs / 1e6, "unit": "MFLUP/s",
             "h2d_bytes_per_step": int(8 * n / done), "d2h_bytes_per_step": int((8 * n + 16 * reads) / done),
-            "seconds": secs}
+            "seconds": secs, "precision": precision}
 
 
 def run_cpu_baseline(target_s=10.0):
@@ -278,7 +368,7 @@ def run_cpu_baseline(target_s=10.0):
             "sample": "%d full steps of the 256^3 periodic box (%.1f s)" % (steps, secs)}
 
 
-def run_sweep(torch, lbm, args, hbm):
+def run_sweep(torch, lbm, args, hbm, pipe):
     """Every scheme x FP64/FP32 x SoA/AoS, and FP16 storage in SoA, on the
     headline workload."""
     out = {}
@@ -296,7 +386,7 @@ def run_sweep(torch, lbm, args, hbm):
                     steps = args.sweep_steps
                     total, per = timed_steps(torch, lat, steps, per_launch=False)
                     mflups = n * steps / total / 1e6
-                    bound, roof = model.bound_roof(variant, False, precision, hbm)
+                    bound, roof = model.bound_roof(variant, False, precision, hbm, pipe)
                     out[key] = {"mflups": round(mflups, 1), "bound": bound, "roof_mflups": round(roof, 1),
                                 "frac": round(mflups / roof, 4),
                                 "bytes_per_flup": model.gpu_bytes(variant, False, precision),
@@ -362,7 +452,7 @@ def run_sparse_solve(torch, lbm, args):
         lat.init()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = permeability.solve(lat, 1.0, 1e-6, max_steps=args.solve_max_steps)
+        res = permeability.solve(lat, 100, 1e-6, max_steps=args.solve_max_steps)
         secs = time.perf_counter() - t0
         n = int(lat.info.nodes)
         out[precision] = {"k": res.k, "steps": res.steps, "converged": res.converged, "seconds": round(secs, 2),
@@ -375,7 +465,7 @@ def run_sparse_solve(torch, lbm, args):
     return out
 
 
-def run_paper_shapes(torch, lbm, args, hbm):
+def run_paper_shapes(torch, lbm, args, hbm, pipe):
     """The paper's benchmark geometries (Sec. 10): the 500x100x100 empty
     channel and a packed bed of spheres with about 2.1 M fluid cells, flow
     along x, walls on y/z; node-list addressing, SoA, TRT (magic 3/16) as the
@@ -398,7 +488,7 @@ def run_paper_shapes(torch, lbm, args, hbm):
                 n = int(lat.info.nodes)
                 mflups = n * args.shape_steps / total / 1e6
                 roof = model.roof_mflups(variant, True, precision, hbm)
-                bound, broof = model.bound_roof(variant, True, precision, hbm, force=True, trt=True)
+                bound, broof = model.bound_roof(variant, True, precision, hbm, pipe, force=True, trt=True)
                 out["%s/%s/%s" % (name, variant, precision)] = {
                     "fluid_nodes": n, "mflups": round(mflups, 1), "frac_of_hbm_roof": round(mflups / roof, 4),
                     "bound": bound, "frac": round(mflups / broof, 4)}
@@ -410,28 +500,23 @@ def run_paper_shapes(torch, lbm, args, hbm):
 
 def run_batch(torch, lbm, args):
     """64 sphere packs, cube sides U{32..192}, porosity U[0.3, 0.8), r = 8
-    (seed 4); FP32 AA pattern on concatenated node lists, launch shape from the
-    autotuner; every geometry advanced in rounds of 100 steps until its flux
-    changes by less than 1e-6 (relative) between rounds, then retired."""
-    from paper_1111_0922_gb300 import permeability
-
+    (seed 4); FP32 on concatenated node lists; the autotuner picks the
+    variant (AA pattern or esoteric twist), block size, nodes per thread and
+    round mode (per-step launches or one persistent launch); every geometry
+    then advances in rounds of 100 steps until the library reports its flux
+    steady (relative change below 1e-6 between rounds), then retires."""
     items = inputs.batch_packs(args.batch_count, seed=4)
-    est = sum(int(it.side ** 3 * it.porosity) for it in items)
-    cap = int(est * 1.15) + 4096 * (len(items) + 1)
-    b = lbm.Batch(cap, variant="aa", precision="f32", max_geometries=len(items) + 1)
+    cap = sum(int(it.side ** 3) for it in items) + 4096 * (len(items) + 1)  # nodes + ghosts <= cells
+    b = lbm.Batch(cap, variant="aa", precision="f32", max_geometries=len(items) + 1, tune_variant=1)
+    g = (1e-6, 0.0, 0.0)
     t0 = time.perf_counter()
-    slots = {}
-    for i, it in enumerate(items):
-        slots[b.admit(it.pack, 1.0, (1e-6, 0.0, 0.0))] = i
+    slots = {b.admit(it.pack, 1.0, g, 1e-6, args.solve_max_steps): i for i, it in enumerate(items)}
     torch.cuda.synchronize()
     t_admit = time.perf_counter() - t0
     nodes_total = b.info.active_nodes
-    bs, npt, tuned = b.tune(rounds=1, k=10)
-    # restart every geometry from rest after tuning: release and re-admit
-    for slot in list(slots):
-        b.release(slot)
-    slots = {b.admit(items[i].pack, 1.0, (1e-6, 0.0, 0.0)): i for i in range(len(items))}
-    prev = {}
+    t0 = time.perf_counter()
+    variant, bs, npt, mode, tuned = b.tune(rounds=1, k=10)  # every geometry restarts from rest
+    t_tune = time.perf_counter() - t0
     done = {}
     updates = 0
     torch.cuda.synchronize()
@@ -441,23 +526,22 @@ def run_batch(torch, lbm, args):
         b.round(100)
         updates += 100 * active_nodes
         for slot in list(slots):
-            _, flux, steps = b.poll(slot)
-            if slot in prev and abs(flux - prev[slot]) < 1e-6 * abs(flux):
-                it = items[slots[slot]]
-                done[slots[slot]] = (permeability.permeability(flux, it.side ** 3, 1.0, 1e-6), steps)
+            state, k, steps = b.poll(slot)
+            if state:
+                done[slots[slot]] = (k, steps, state == 1)
                 b.release(slot)
                 del slots[slot]
-            else:
-                prev[slot] = flux
     secs = time.perf_counter() - t1
     b.close()
     steps = [v[1] for v in done.values()]
-    return {"workload": "64 sphere packs, side U{32..192}, porosity U[0.3,0.8), r = 8 (seed 4), FP32 AA, "
+    return {"workload": "64 sphere packs, side U{32..192}, porosity U[0.3,0.8), r = 8 (seed 4), FP32, "
                         "rounds of 100 steps, retire at relative flux change < 1e-6",
             "geometries": len(items), "fluid_nodes": int(nodes_total), "admit_s": round(t_admit, 2),
-            "tuned": {"block_size": bs, "nodes_per_thread": npt, "mflups": round(tuned, 1)},
-            "converged": len(done), "unfinished": len(items) - len(done), "solve_wall_s": round(secs, 2),
-            "aggregate_mflups": round(updates / secs / 1e6, 1),
+            "tuned": {"variant": "aa" if variant == lbm.LBM_AA else "et", "block_size": bs, "nodes_per_thread": npt,
+                      "round_mode": "persistent" if mode == 1 else "per-step launches",
+                      "mflups": round(tuned, 1), "tune_s": round(t_tune, 2)},
+            "converged": sum(1 for v in done.values() if v[2]), "unfinished": len(items) - len(done),
+            "solve_wall_s": round(secs, 2), "aggregate_mflups": round(updates / secs / 1e6, 1),
             "steps_to_converge": {"min": min(steps) if steps else None, "median": float(np.median(steps)) if steps else None,
                                   "max": max(steps) if steps else None},
             "k_range": [min(v[0] for v in done.values()), max(v[0] for v in done.values())] if done else None}
@@ -467,7 +551,9 @@ def run_serving(torch, lbm, args):
     """Poisson arrivals (20 requests/s, seed 5) of sphere packs with sides
     U{64..384} and porosity U[0.3, 0.8), r = 8, served by continuous batching
     with FP16-stored PDFs (FP32 collision, FP64 flux sums) within a 150 GB HBM
-    budget; the first requests also solved one at a time in FP64."""
+    budget; then the same requests' smallest few (by fluid nodes, named in
+    the output) solved one at a time with FP64 storage and arithmetic, for a
+    like-for-like comparison of service time and permeability."""
     from paper_1111_0922_gb300 import permeability, serving
 
     budget = 150e9
@@ -481,28 +567,38 @@ def run_serving(torch, lbm, args):
     eng.close()
     torch.cuda.empty_cache()
     summ = st.summary()
-    # FP64, one solve at a time, on the first requests
+    by_id = {x.rid: x for x in st.results}
+    # the matched subset: the requests with the fewest fluid nodes
+    served = sorted((x for x in st.results if x.nodes > 0), key=lambda x: x.nodes)
+    subset = [x.rid for x in served[: args.serve_fp64]]
     base = []
-    for r in reqs[: args.serve_fp64]:
+    for rid in subset:
+        r = reqs[rid]
         lat = lbm.Lattice(r.pack.dims, r.pack.periodic, variant="aa", addressing="indirect", precision="f64",
                           omega=r.omega, force=r.force)
         t0 = time.perf_counter()
         lat.set_geometry_spheres(r.pack.centres, r.pack.radius, r.pack.unit)
         lat.init()
-        res = permeability.solve(lat, r.omega, r.force[0], max_steps=args.serve_max_steps)
-        base.append((r.rid, res.k, time.perf_counter() - t0, res.steps))
+        res = permeability.solve(lat, 100, 1e-6, max_steps=args.serve_max_steps)
+        base.append((rid, res.k, time.perf_counter() - t0, res.steps, res.converged))
         lat.close()
         torch.cuda.empty_cache()
-    by_id = {x.rid: x for x in st.results}
-    k_err = [abs(by_id[rid].k - k) / k for rid, k, _, _ in base if rid in by_id and by_id[rid].converged]
+    k_err = {rid: abs(by_id[rid].k - k) / k for rid, k, _, _, _ in base if by_id[rid].converged}
+    fp16_service = [by_id[rid].finished - by_id[rid].admitted for rid in subset]
     return {"workload": "Poisson 20/s (seed 5), %d requests, side U{64..384}, porosity U[0.3,0.8), r = 8, "
                         "AA pattern, FP16 storage (S = 2^26), 150 GB budget" % len(reqs),
             "offered_node_rate_per_s": round(offered, 1), "capacity_slots": cap,
             **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()},
-            "fp64_one_at_a_time": {"requests": len(base),
-                                   "mean_service_s": round(float(np.mean([b[2] for b in base])), 3) if base else None,
-                                   "solves_per_s": round(len(base) / sum(b[2] for b in base), 4) if base else None,
-                                   "k_rel_err_fp16_vs_fp64_max": max(k_err) if k_err else None}}
+            "matched_subset": {
+                "request_ids": subset, "fluid_nodes": [by_id[rid].nodes for rid in subset],
+                "fp64_one_at_a_time": {
+                    "service_s": [round(b[2], 3) for b in base], "steps": [b[3] for b in base],
+                    "solves_per_s": round(len(base) / sum(b[2] for b in base), 4) if base else None},
+                "fp16_batched": {
+                    "service_s": [round(t, 3) for t in fp16_service], "steps": [by_id[rid].steps for rid in subset],
+                    "latency_s": [round(by_id[rid].latency, 3) for rid in subset]},
+                "k_rel_err_fp16_vs_fp64": {str(r): float("%.3g" % e) for r, e in k_err.items()},
+                "k_rel_err_max": max(k_err.values()) if k_err else None}}
 
 
 def main_gb300(args):
@@ -521,28 +617,32 @@ def main_gb300(args):
     build.build()
     lbm.load()
     hbm, peak_kind = measured_peaks()
-    head = run_headline(torch, lbm, args, rank, world)
+    dev = torch.cuda.current_device()
+    head = run_headline(torch, lbm, args, rank, world, "f64")
     n = head["nodes"]
     value = replica_value(n, args.steps, world, head["total_s"])
-    bytes_launch = n * model.kernel_bytes_per_flup("aa", False, "f32")
-    achieved = bytes_launch / head["per_launch_s"] / 1e9
-    traffic = profiled_traffic("aa_f32_soa_direct_256")
+    pipe = fp64_pipe(torch, dev, head["clocks"])
+    roof = fp64_roofline(head, pipe, hbm, peak_kind)
+    by_prec = {}
+    if not args.no_side:
+        for prec in ("f32", "f16s"):
+            side = run_headline(torch, lbm, args, rank, world, prec, sample_clocks=False)
+            by_prec[prec] = hbm_roofline(side, hbm, peak_kind, args.steps)
+            by_prec[prec]["gpu_launches"] = side["kernels"]
+    roof["by_precision"] = by_prec
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": "MFLUP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(head["total_s"] / args.steps * 1e3, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": "aa", "precision": "f32 (f - w stored)",
-                   "layout": "soa" + (", cells z and z + nz/2 paired in 8-byte words" if head["paired"] else ""),
-                   "addressing": "direct", "nodes_per_gpu": n,
+        "config": {"workload": WORKLOAD, "variant": "aa", "precision": "f64 (f - w stored, FP64 collision)",
+                   "layout": "soa", "addressing": "direct", "nodes_per_gpu": n,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "state 1.27 GB > 129 MB L2, no flush needed"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                     "bytes_per_launch": int(bytes_launch), "traffic": traffic,
-                     "kernel": ("k_aa_even_zp/k_aa_odd_zp<CodecF32>" if head["paired"]
-                                else "k_aa_even/k_aa_odd<CodecF32,SoA,direct>")},
+                   "l2": "state 2.55 GB > 129 MB L2, no flush needed",
+                   "side_runs": "roofline.by_precision: the same workload with FP32 and FP16 storage "
+                                "(FP32 collision), timed the same way after the headline"},
+        "roofline": roof,
         "gpu_launches": head["kernels"],
         "clocks": head["clocks"],
     }
@@ -551,19 +651,20 @@ def main_gb300(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = run_cpu_baseline(args.cpu_seconds)
     if rank == 0 and not args.no_sweep:
-        result["variants"] = run_sweep(torch, lbm, args, hbm)
+        result["variants"] = run_sweep(torch, lbm, args, hbm, pipe)
     if rank == 0 and not args.no_sparse:
         result["sparse"] = run_sparse(torch, lbm, args, hbm)
         if not args.no_solve:
             result["sparse"]["steady_flux"] = run_sparse_solve(torch, lbm, args)
     if rank == 0 and not args.no_shapes:
-        result["paper_shapes"] = run_paper_shapes(torch, lbm, args, hbm)
+        result["paper_shapes"] = run_paper_shapes(torch, lbm, args, hbm, pipe)
     if rank == 0 and not args.no_batch:
         result["batch"] = run_batch(torch, lbm, args)
         log("batch", result["batch"])
     if rank == 0 and not args.no_serving:
         result["serving"] = run_serving(torch, lbm, args)
         log("serving", result["serving"])
+    result["roofline"]["per_variant"] = per_variant_table(result)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -571,10 +672,27 @@ def main_gb300(args):
         print(json.dumps(result), flush=True)
 
 
+def per_variant_table(result):
+    """Compact table of every measured row: {name: [MFLUP/s, fraction of its
+    own roof]} (full grid: scheme/precision/layout; node lists: sparse/...,
+    paper shapes: channel/... and bed/...)."""
+    table = {}
+    for key, row in result.get("variants", {}).items():
+        if "mflups" in row:
+            table[key] = [row["mflups"], row["frac"]]
+    for key, row in result.get("sparse", {}).items():
+        if isinstance(row, dict) and "mflups" in row and "frac" in row:
+            table["sparse/" + key] = [row["mflups"], row["frac"]]
+    for key, row in result.get("paper_shapes", {}).items():
+        table[key] = [row["mflups"], row["frac"]]
+    return table
+
+
 def main_reference(args):
-    """The FP64 CPU oracle on the host cores, same workload and metric; each
-    step is one oracle step over a bounded sample: a 256 x 256 x 16 periodic
-    slab cut from the same initial state."""
+    """The FP64 CPU oracle on the host cores, same workload, metric and
+    arithmetic: each step is one oracle step (the push definition, OpenMP
+    over cells) of the whole periodic 256^3 box from the same initial state
+    (about 0.2 s per step on 16 cores)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -583,19 +701,18 @@ def main_reference(args):
 
     oracle.build()
     threads = oracle.default_threads()
-    dims = (256, 256, 16)
-    rho = inputs.density_noise(DIMS, seed=SEED)[: int(np.prod(dims))]
+    rho = inputs.density_noise(DIMS, seed=SEED)
     _, w = oracle.lattice()
     f = np.ascontiguousarray(w[:, None] * rho[None, :])
     for _ in range(args.warmup):
-        f = oracle.push_full(dims, (1, 1, 1), None, f, OMEGA, nthreads=threads)
+        f = oracle.push_full(DIMS, (1, 1, 1), None, f, OMEGA, nthreads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f = oracle.push_full(dims, (1, 1, 1), None, f, OMEGA, nthreads=threads)
+        f = oracle.push_full(DIMS, (1, 1, 1), None, f, OMEGA, nthreads=threads)
     secs = time.perf_counter() - t0
-    n = int(np.prod(dims))
+    n = int(np.prod(DIMS))
     value = n * args.steps / secs / 1e6
-    sample = "each step: one oracle step of a 256x256x16 periodic slab (%d nodes) of the workload" % n
+    sample = "each step: one oracle step of the whole 256^3 periodic box (%d nodes)" % n
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MFLUP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -620,6 +737,7 @@ def parse(argv=None):
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the FP32 / FP16 headline side runs")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--sparse-steps", type=int, default=50)
     ap.add_argument("--no-solve", action="store_true")
@@ -630,8 +748,8 @@ def parse(argv=None):
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-seconds", type=float, default=60.0)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=16)
-    ap.add_argument("--serve-fp64", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-fp64", type=int, default=4)
     ap.add_argument("--serve-max-steps", type=int, default=30000)
     a = ap.parse_args(argv)
     if a.warmup < 3:

@@ -102,9 +102,6 @@ typedef struct lbm_config {
   int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes, k extra
                                 planes of storage; 0 = slabs of about 2^22 cells);
                                 node list: slab size B >= 1 nodes (0 = 2^21) */
-  int32_t pair_x;            /* LBM_AA, full grid, SoA: 1 = two x-adjacent nodes per thread with vector
-                                accesses where possible (periodic x, even nx, no solid cell);
-                                0 = one node per thread (default, faster on GB300) */
   int32_t store_hint;        /* LBM_OS_PUSH / LBM_OS_PULL, SoA: 1 = write the second lattice with
                                 cache-streaming (evict-first) stores, the GPU counterpart of the
                                 non-temporal stores of OS-NT (Sec. 3); 0 = ordinary stores */
@@ -116,7 +113,7 @@ typedef struct lbm_config {
                                 links, then one pass completes the links between tiles;
                                 0 = default: 1 (measured fastest on GB300) */
   int32_t pair_z;            /* Cell pairs, LBM_F16S or LBM_F32 storage, SoA, full grid without
-                                solid cells, pair_x 0: LBM_AA, LBM_TS, LBM_OS_PUSH / PULL
+                                solid cells: LBM_AA, LBM_TS, LBM_OS_PUSH / PULL
                                 (store_hint 0) and LBM_ET (periodic box) keep cells z and z + nz/2
                                 (even nz) in one word per array (4 bytes FP16, 8 bytes FP32), and
                                 one thread updates both; LBM_CG pairs cells y and y + ny/2 instead
@@ -149,96 +146,142 @@ typedef struct lbm_info {
 typedef struct lbm lbm_t;
 
 /* Fill *cfg with defaults: 32^3 periodic box, LBM_AA, direct, SoA, FP32,
- * omega 1, no force, default launch shape, default stream, cudaMalloc. */
+ * omega 1, no force, default launch shape, default stream, cudaMalloc.
+ * (Configuration only; the D3Q19 lattice itself is Sec. 1.) */
 lbm_status lbm_config_default(lbm_config *cfg);
 
-/* Validate cfg and create a handle on the current CUDA device.  No geometry
- * yet: call lbm_set_geometry or lbm_set_geometry_spheres next. */
+/* Validate cfg and create a handle on the current CUDA device: one lattice
+ * of PDF arrays, or two for the two-lattice schemes (LBM_TS, LBM_OS_*,
+ * Sec. 2-3; the others keep one, Sec. 4-7).  No geometry yet: call
+ * lbm_set_geometry or lbm_set_geometry_spheres next.  Errors:
+ * LBM_ERR_INVALID_ARG for an invalid configuration, LBM_ERR_UNSUPPORTED for
+ * a valid combination the library does not build, LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_config *cfg, lbm_t **out);
 
-/* Free every device buffer (waits for the handle's stream).  NULL is OK. */
+/* Free every device buffer (waits for the handle's stream).  NULL is OK.
+ * (Resource release; no counterpart in the paper.) */
 lbm_status lbm_destroy(lbm_t *h);
 
-/* One-line description of the last failure on h (or a global one if h is NULL). */
+/* One-line description of the last failure on h (or a global one if h is
+ * NULL), and the name of a status.  (Diagnostics; no counterpart.) */
 const char *lbm_last_error(const lbm_t *h);
 const char *lbm_status_string(lbm_status s);
 
-/* Geometry (Sec. 1; the packed bed of Fig. 7, Sec. 10).  solid_mask_host:
- * nx*ny*nz bytes, x fastest, nonzero = solid, or NULL for an all-fluid box.
- * Builds on the GPU the fluid-node list (lexicographic) and, for
- * LBM_INDIRECT, IDX[18][N] (IDX[i-1][k] = node reached from node k along
- * c_i, -1 for a solid or wall link) plus the variant's own index data;
- * allocates the PDF storage.  Resets the state to rest (f = w). Synchronises. */
+/* Geometry (Sec. 1: a full grid or the sparse representation of the fluid
+ * nodes with an adjacency list; the packed bed of Fig. 7, Sec. 10).
+ * solid_mask_host: nx*ny*nz bytes, x fastest, nonzero = solid, or NULL for
+ * an all-fluid box; borrowed for the call.  Builds on the GPU the fluid-node
+ * list (lexicographic) and, for LBM_INDIRECT, IDX[18][N] (IDX[i-1][k] = node
+ * reached from node k along c_i, -1 for a solid or wall link) plus the
+ * variant's own index data; allocates the PDF storage.  Resets the state to
+ * rest (f = w).  Synchronises.  LBM_ERR_OOM when the storage does not fit. */
 lbm_status lbm_set_geometry(lbm_t *h, const uint8_t *solid_mask_host);
 
-/* Same, with the solid mask generated on the GPU from overlapping spheres:
- * a cell is solid iff the minimum-image distance (periodic axes) between its
- * centre and some sphere centre is <= radius.  centres_host: nsph x 3 int64
- * positions and the radius in units of 1/unit cells (exact integer test). */
+/* Same, with the solid mask generated on the GPU from overlapping spheres
+ * (the packed bed of spheres of Sec. 10, Fig. 7): a cell is solid iff the
+ * minimum-image distance (periodic axes) between its centre and some sphere
+ * centre is <= radius.  centres_host: nsph x 3 int64 positions and the
+ * radius in units of 1/unit cells (exact integer test). */
 lbm_status lbm_set_geometry_spheres(lbm_t *h, int64_t nsph, const int64_t *centres_host,
                                     int64_t radius, int64_t unit);
 
-/* Read back geometry: the solid mask (nx*ny*nz bytes), the node list
- * (node -> cell, N int32) and IDX (18*N int32, direction-major).  Host
- * buffers.  lbm_get_idx is valid for LBM_INDIRECT only.  Synchronise. */
+/* Read back geometry (Sec. 1: the node list and its adjacency array IDX):
+ * the solid mask (nx*ny*nz bytes), the node list (node -> cell, N int32)
+ * and IDX (18*N int32, direction-major).  Host buffers the caller owns.
+ * lbm_get_idx is valid for LBM_INDIRECT only (else LBM_ERR_STATE).
+ * Synchronise. */
 lbm_status lbm_get_mask(lbm_t *h, uint8_t *mask_host);
 lbm_status lbm_get_nodes(lbm_t *h, int32_t *cells_host);
 lbm_status lbm_get_idx(lbm_t *h, int32_t *idx_host);
 lbm_status lbm_get_info(const lbm_t *h, lbm_info *info);
 
-/* Initial state f_i = f_eq(rho, u) per node (direct: per cell, solid cells
- * ignored).  rho: n doubles or NULL (= 1); u: 3n doubles (x,y,z per node) or
- * NULL (= 0).  on_device = 1: the pointers are device memory.  Pull-type
- * schemes store the pre-image of this state under streaming.  Step count 0. */
+/* Initial state f_i = f_eq(rho, u) per node (the equilibrium of the
+ * collision, Sec. 1; direct: per cell, solid cells ignored).  rho: n doubles
+ * or NULL (= 1); u: 3n doubles (x,y,z per node) or NULL (= 0).  on_device =
+ * 1: the pointers are device memory.  Each scheme stores it in its own form:
+ * pull-type schemes (Sec. 3-4) the pre-image under streaming, the esoteric
+ * twist its shifted arrays (Sec. 7).  Step count 0. */
 lbm_status lbm_init(lbm_t *h, const double *rho, const double *u, int on_device);
 
-/* Set / get the natural state f[i * n + k] (FP64, n = nodes or cells).
- * get requires a natural state (LBM_AA: even step count) else LBM_ERR_STATE;
- * solid cells of a direct grid read back as 0.  get synchronises. */
+/* Set / get the natural state f[i * n + k] (FP64, n = nodes or cells),
+ * mapped to and from each scheme's storage (Sec. 2-7).  get requires a
+ * natural state (LBM_AA: even step count, Sec. 6) else LBM_ERR_STATE; solid
+ * cells of a direct grid read back as 0.  get synchronises. */
 lbm_status lbm_set_pdfs(lbm_t *h, const double *f, int on_device);
 lbm_status lbm_get_pdfs(lbm_t *h, double *f, int on_device);
 
-/* Enqueue n >= 0 time steps on cfg->stream; returns without waiting. */
+/* Enqueue n >= 0 time steps (collision and propagation, Sec. 1) by the
+ * configured scheme (Sec. 2-7) on cfg->stream; returns without waiting.
+ * LBM_ERR_STATE without a geometry. */
 lbm_status lbm_step(lbm_t *h, int n);
 
 /* Enqueue n >= 1 steps; the first kernel also reduces, in FP64 with a fixed
  * summation order, the mass sum(rho) and the flux sum(rho u_x) of the state
- * the call starts from, over all fluid nodes.  Requires a natural starting
- * state.  mass / jx are host pointers; the call synchronises. */
+ * the call starts from, over all fluid nodes (the flow quantities of the
+ * porous-media solver of Sec. 10; the paper gives no formula).  Requires a
+ * natural starting state.  mass / jx are host pointers; synchronises. */
 lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx);
 
-/* Mass and flux of the current (natural) state, FP64, fixed order.  Syncs. */
+/* Mass and flux of the current (natural) state, FP64, fixed order (as
+ * lbm_step_flux).  Synchronises. */
 lbm_status lbm_flux(lbm_t *h, double *mass, double *jx);
 
-/* Density (n) and velocity (3n) of the current natural state; either
- * pointer may be NULL.  Synchronises when on_device = 0. */
+/* Density (n) and velocity (3n) of the current natural state, the moments
+ * of the collision (Sec. 1); either pointer may be NULL.  Synchronises when
+ * on_device = 0. */
 lbm_status lbm_macroscopics(lbm_t *h, double *rho, double *u, int on_device);
 
 /* Wait for the handle's stream and report device-side errors. */
 lbm_status lbm_sync(lbm_t *h);
 
+/* Steady flow through a porous geometry and its permeability (the flow
+ * through packed beds the paper's solver is built for, Sec. 10; Darcy's
+ * law, which the paper does not state).  From the current state, runs rounds
+ * of `check` steps (even, >= 2) with lbm_step_flux until the flux sum(rho
+ * u_x) of two consecutive rounds differs by less than tol * |flux| (tol >=
+ * 0), or until max_steps (>= check) steps are done.  Outputs (host pointers,
+ * each may be NULL): permeability k = nu <rho u_x> / g_x with the average
+ * over every cell of the box and nu = (1/omega - 1/2)/3 (NaN when g_x = 0),
+ * the last round's mass and flux, and the steps done.  Returns LBM_OK when
+ * steady, LBM_ERR_NOT_CONVERGED (outputs still written) at the step cap. */
+lbm_status lbm_solve_permeability(lbm_t *h, int32_t check, double tol, int64_t max_steps, double *permeability,
+                                  double *mass, double *flux, int64_t *steps);
+
 /* ------------------------------------------------------------------------
- * Batches: many geometries advanced together (continuous batching).
+ * Batches: many geometries advanced together (continuous batching; the
+ * paper solves one geometry at a time, Sec. 10, so this layer has no
+ * counterpart there, while every step of it is the node-list AA pattern of
+ * Sec. 6 or esoteric twist of Sec. 7).
  *
  * Each admitted geometry is a fluid-node list stored as one segment of
  * shared SoA arrays (segments start on multiples of 4096 slots; IDX entries
- * are absolute slot numbers).  One launch per time step covers the nodes of
+ * are absolute slot numbers).  One round of k steps covers the nodes of
  * every active geometry, each with its own omega, force and step count, so
- * geometries admitted at different times run side by side.  A round of k
- * steps is replayed from a captured CUDA graph; its first step also reduces
- * each geometry's mass and flux (FP64, per 4096-aligned chunk, then summed in
- * chunk order), so a geometry's results are bit-identical alone and in any
- * mix.  Variants: LBM_AA or LBM_ET on node lists, SoA. */
+ * geometries admitted at different times run side by side.  A round is
+ * replayed from a captured CUDA graph: one launch per step, or one
+ * persistent cooperative launch for all k steps (round_mode).  Its first
+ * step also reduces each geometry's mass and flux (FP64, per 4096-aligned
+ * chunk, then summed in chunk order), so a geometry's results are
+ * bit-identical alone and in any mix, in either round mode.  After each
+ * round the library applies each geometry's steady-flux test (relative flux
+ * change between consecutive rounds below its tol) and computes its
+ * permeability.  Admissions build their geometry on a second stream, so
+ * they overlap a round in flight; the next round waits for them. */
 typedef struct lbm_batch_config {
-  int32_t variant;           /* LBM_AA or LBM_ET */
+  int32_t variant;           /* LBM_AA or LBM_ET (the starting variant when tune_variant = 1) */
   int32_t precision;         /* LBM_F64, LBM_F32, LBM_F16S */
-  int32_t block_size;        /* threads per block, multiple of 32, <= 256; 0 = 256 */
+  int32_t block_size;        /* threads per block: 64, 128, 256 or 512; 0 = 256 */
   int32_t nodes_per_thread;  /* 1, 2, 4 or 8; block_size * nodes_per_thread divides 4096; 0 = 1 */
   int64_t capacity_slots;    /* node slots of the shared arrays (rounded up to 4096) */
   int32_t max_geometries;    /* size of the geometry table */
   int32_t keep_idx;          /* LBM_AA: 1 = IDX keeps -1 for solid links; 0 = bounce-back slots
                                 folded into IDX when the capacity is below 2^30 (faster) */
   double f16_scale;          /* LBM_F16S: the power-of-two scale of every geometry */
+  int32_t tune_variant;      /* 1 = lbm_batch_tune may switch the batch between LBM_AA and LBM_ET
+                                (index arrays sized for both: 18 words per slot); 0 = fixed */
+  int32_t round_mode;        /* 0 = one launch per step in the round's graph; 1 = one persistent
+                                cooperative launch per round (grid-wide barrier between steps with
+                                a bounded wait: LBM_ERR_TIMEOUT instead of a hang) */
   void *stream;              /* cudaStream_t; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator, as in lbm_config */
   lbm_free_fn dev_free;
@@ -254,52 +297,80 @@ typedef struct lbm_batch_info {
   int32_t active_geometries;
   int32_t block_size;
   int32_t nodes_per_thread;
-  int32_t work_chunks;       /* blocks of one step launch */
+  int32_t work_chunks;       /* chunks of block_size * nodes_per_thread nodes per step */
+  int32_t variant;           /* LBM_AA or LBM_ET, as tuned */
+  int32_t round_mode;        /* as tuned */
 } lbm_batch_info;
 
 typedef struct lbm_batch lbm_batch_t;
 
 /* Device bytes per node slot of a batch: 19 PDFs + the index words
- * (18 for LBM_AA, 9 for LBM_ET). */
+ * (18 for LBM_AA or a batch whose variant may be tuned, 9 for LBM_ET;
+ * Tab. 5 and Tab. 6 count the words each step reads). */
 int64_t lbm_batch_bytes_per_slot(int32_t variant, int32_t precision);
 
-/* Allocate the shared arrays (capacity_slots x lbm_batch_bytes_per_slot). */
+/* Allocate the shared arrays (capacity_slots x bytes per slot).
+ * LBM_ERR_OOM when they do not fit. */
 lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out);
 lbm_status lbm_batch_destroy(lbm_batch_t *b);
 const char *lbm_batch_last_error(const lbm_batch_t *b);
 
-/* Admit a sphere-pack geometry (as lbm_set_geometry_spheres: dims[3],
- * periodic[3], nsph x 3 centres and radius in 1/unit cells), with its own
- * omega and force, at rest.  Builds its node list and index on the GPU into
- * the first free range that fits; LBM_ERR_OOM (nothing changed) when no range
- * or geometry-table entry is free.  *slot receives its id.  Synchronises. */
+/* Admit a geometry given as a solid mask (nx*ny*nz bytes on the host, x
+ * fastest, nonzero = solid; copied, so the caller may free it on return),
+ * periodic[3] as in lbm_config, with its own omega, force[3], steady-flux
+ * tolerance tol (>= 0) and step cap max_steps (<= 0: none), at rest.  Builds
+ * its node list and index (Sec. 1; Tab. 5 / Tab. 6 layout) on the GPU into
+ * the first free range that fits.  LBM_ERR_OOM (nothing changed) when no
+ * range or geometry-table entry is free.  *slot receives its id.  Returns
+ * once the geometry is built; its device work may still overlap a round in
+ * flight. */
+lbm_status lbm_batch_admit(lbm_batch_t *b, const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
+                           const int32_t *periodic, double omega, const double *force, double tol,
+                           int64_t max_steps, int32_t *slot);
+
+/* The same for a sphere pack (the packed bed of Sec. 10, Fig. 7), as
+ * lbm_set_geometry_spheres: dims[3], periodic[3], nsph x 3 centres and the
+ * radius in 1/unit cells. */
 lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const int32_t *periodic, int64_t nsph,
                                    const int64_t *centres, int64_t radius, int64_t unit, double omega,
-                                   const double *force, int32_t *slot);
+                                   const double *force, double tol, int64_t max_steps, int32_t *slot);
 
-/* Free a geometry's range and table entry. */
+/* Free a geometry's range and table entry (waits for a round in flight). */
 lbm_status lbm_batch_release(lbm_batch_t *b, int32_t slot);
 
-/* Enqueue k >= 1 steps of every active geometry (graph replay).  The mass
- * and flux of each geometry's state at the start of the round become
- * readable with lbm_batch_poll.  Asynchronous. */
+/* Enqueue k >= 1 steps of every active geometry (graph replay).
+ * Asynchronous; the results become readable with lbm_batch_poll. */
 lbm_status lbm_batch_round(lbm_batch_t *b, int32_t k);
 
-/* Results of the last round for one geometry, and its step count.  Waits for
- * the round. */
-lbm_status lbm_batch_poll(lbm_batch_t *b, int32_t slot, double *mass, double *flux, int64_t *steps);
+/* State of one geometry after the last completed round (waits for a round
+ * in flight): *done = 0 running, 1 steady (the flux of the state the last
+ * round started from differs from the previous round's by less than tol
+ * times its magnitude), 2 stopped at max_steps without reaching it;
+ * *permeability = nu <rho u_x> / g_x from that flux, the average over every
+ * cell of the geometry's box (Darcy's law; NaN when g_x = 0); *steps done.
+ * Any output pointer may be NULL.  LBM_ERR_TIMEOUT if a persistent round's
+ * grid barrier gave up. */
+lbm_status lbm_batch_poll(lbm_batch_t *b, int32_t slot, int32_t *done, double *permeability, int64_t *steps);
+
+/* FP64 mass sum(rho) and flux sum(rho u_x) of the state the last completed
+ * round started from, and the steps done (waits for a round in flight). */
+lbm_status lbm_batch_flux(lbm_batch_t *b, int32_t slot, double *mass, double *flux, int64_t *steps);
 lbm_status lbm_batch_slot_info(lbm_batch_t *b, int32_t slot, int64_t *nodes, int64_t *cells, int64_t *steps);
 lbm_status lbm_batch_get_info(lbm_batch_t *b, lbm_batch_info *info);
 
-/* Natural state of one geometry (19 x nodes FP64, host); LBM_AA requires an
- * even step count.  Synchronises. */
+/* Natural state of one geometry (19 x nodes FP64, host; the AA pattern's
+ * read-out after an even step count, Sec. 6, else LBM_ERR_STATE; the
+ * esoteric twist's array map, Sec. 7).  Synchronises. */
 lbm_status lbm_batch_get_pdfs(lbm_batch_t *b, int32_t slot, double *f_host);
 
-/* Launch-shape autotuner: times `rounds` rounds of k steps for each
- * (block size, nodes per thread) candidate with CUDA events and keeps the
- * fastest.  Advances the active geometries by those steps. */
-lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *best_block_size,
-                          int32_t *best_nodes_per_thread, double *best_mflups);
+/* Autotuner: times `rounds` rounds of k steps with CUDA events for every
+ * candidate (variant: LBM_AA and LBM_ET when tune_variant = 1, else the
+ * configured one; block size 128, 256, 512; nodes per thread 1, 2, 4, 8;
+ * round mode 0 and 1) on the active geometries and keeps the fastest.
+ * Every active geometry restarts from rest (step 0) in the chosen
+ * configuration.  Outputs may be NULL. */
+lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *best_variant, int32_t *best_block_size,
+                          int32_t *best_nodes_per_thread, int32_t *best_round_mode, double *best_mflups);
 
 /* Mass and flux of a caller-owned natural PDF array, with no allocation.
  * (This entry point has no counterpart in the paper.)
@@ -321,20 +392,26 @@ lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *be
  *   gx         body acceleration along x (the flux is sum rho u_x with
  *              u = (sum c f + rho g / 2) / rho, as lbm_flux)
  *   out_dev    device pointer to 2 doubles: sum rho, sum rho u_x (FP64,
- *              fixed summation order: node chunks of LBM_NOALLOC_CHUNK)
+ *              fixed summation order: block b sums nodes [b c, (b+1) c) with
+ *              the chunk c = ceil(n / LBM_NOALLOC_MAX_BLOCKS) rounded up to
+ *              a multiple of 256, at least LBM_NOALLOC_MIN_CHUNK, so the
+ *              order, and the result's bits, depend on n alone)
  *   stream     cudaStream_t to enqueue on (NULL = default stream)
  *
- * Limits and errors: n must be in [1, LBM_NOALLOC_MAX_BLOCKS *
- * LBM_NOALLOC_CHUNK] (2^30 nodes), else LBM_ERR_INVALID_ARG; bad pointers or
- * enums give LBM_ERR_INVALID_ARG; a launch failure gives LBM_ERR_CUDA.
- * The first call on a device looks up the scratch's device address (a
- * one-time set-up per device, done with that device current); make that first
- * call before any stream capture.  All calls share the one scratch array and
- * each rewrites the partials it reads: calls that may overlap on the GPU
- * (other streams or threads) race on it and must be ordered by the caller.
- * Asynchronous: the result is in out_dev once the stream reaches it. */
+ * Limits and errors: n must be in [1, LBM_NOALLOC_MAX_NODES] (2^30 nodes),
+ * else LBM_ERR_INVALID_ARG; bad pointers or enums give LBM_ERR_INVALID_ARG; a
+ * launch failure gives LBM_ERR_CUDA.  Every call made outside a stream
+ * capture looks up the scratch's device address with the device current
+ * (so a context created anew on the device is always served correctly); a
+ * call under capture reuses the address of the device's last call, so make
+ * one call on each device before capturing (else LBM_ERR_CUDA).  All calls
+ * share the one scratch array and each rewrites the partials it reads:
+ * calls that may overlap on the GPU (other streams or threads) race on it
+ * and must be ordered by the caller.  Asynchronous: the result is in out_dev
+ * once the stream reaches it. */
 #define LBM_NOALLOC_MAX_BLOCKS 16384
-#define LBM_NOALLOC_CHUNK 65536
+#define LBM_NOALLOC_MIN_CHUNK 4096
+#define LBM_NOALLOC_MAX_NODES (LBM_NOALLOC_MAX_BLOCKS * (int64_t)65536)
 lbm_status lbm_flux_noalloc(const void *f_dev, int32_t precision, int32_t layout, int64_t n, int64_t npad,
                             double f16_scale, double gx, double *out_dev, void *stream);
 

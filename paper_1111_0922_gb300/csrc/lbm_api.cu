@@ -268,13 +268,6 @@ static LaunchShape shape_of(const lbm_t *h) {
 
 static int64_t blocks_of(const LaunchShape &L) { return (int64_t)L.grid.x * L.grid.y * L.grid.z; }
 
-// AA pattern with two x-adjacent nodes per thread (lbm_pair.cuh)?
-static bool use_pairs(const lbm_t *h) {
-  const lbm_config &c = h->cfg;
-  return c.variant == LBM_AA && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 1 &&
-         c.periodic[0] && (c.nx % 2) == 0 && !h->any_solid && h->grid.hx == 0;
-}
-
 // FP16 / FP32 storage in z pairs (Grid::zpair, kernels in lbm_steps.cuh and
 // lbm_swap.cuh)?  Two-step, one-step and AA pattern on a full grid without
 // solid cells or halos, the esoteric twist on a periodic one, the coloured
@@ -289,7 +282,7 @@ static bool use_zpairs(const lbm_t *h) {
                       (c.variant == LBM_SWAP && c.periodic[2] && c.swap_schedule <= 1 && (c.nz % 4) == 0 &&
                        c.nz >= 8);
   const bool prec = c.precision == LBM_F16S || c.precision == LBM_F32;
-  return scheme && prec && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_x == 0 && c.pair_z != 2 &&
+  return scheme && prec && c.addressing == LBM_DIRECT && c.layout == LBM_SOA && c.pair_z != 2 &&
          (c.nz % 2) == 0 && !h->any_solid && h->grid.hx == 0 && h->grid.hy == 0 && h->grid.hz == 0;
 }
 
@@ -311,20 +304,6 @@ static LaunchShape zpair_shape_of(const lbm_t *h) {
                       ? h->cfg.nodes_per_thread
                       : ((h->cfg.variant == LBM_AA && h->cfg.precision == LBM_F16S) ? 4 : 2);
   L.grid.z = (unsigned)std::min<int64_t>((h->cfg.nz / 2 + npt - 1) / npt, 65535);
-  return L;
-}
-
-static LaunchShape pair_shape_of(const lbm_t *h) {
-  LaunchShape L;
-  const int bs = h->cfg.block_size > 0 ? h->cfg.block_size : 128;
-  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 1;
-  const int npairs = h->cfg.nx / 2;
-  const int bx = (int)std::min<int64_t>(bs, round_up(npairs, 32));
-  const int by = std::max(1, bs / bx);
-  L.grid = dim3((unsigned)((npairs + bx - 1) / bx), (unsigned)((h->cfg.ny + by - 1) / by),
-                (unsigned)std::min<int64_t>((h->cfg.nz + npt - 1) / npt, 65535));
-  L.block = dim3((unsigned)bx, (unsigned)by);
-  L.stream = h->stream;
   return L;
 }
 
@@ -425,7 +404,6 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->dev_alloc && !cfg->dev_free) return fail(nullptr, LBM_ERR_INVALID_ARG, "dev_alloc without dev_free");
   if (cfg->cg_shift < 0 || (cfg->addressing == LBM_DIRECT && cfg->cg_shift == 1))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "cg_shift: >= 2 planes on a full grid, >= 1 node on a node list");
-  if (cfg->pair_x != 0 && cfg->pair_x != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_x must be 0 or 1");
   if (cfg->pair_z < 0 || cfg->pair_z > 2) return fail(nullptr, LBM_ERR_INVALID_ARG, "pair_z must be 0 .. 2");
   if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
   if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
@@ -437,9 +415,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   h->cfg = *cfg;
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) {
     delete h;
-    return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    return fail(nullptr, LBM_ERR_CUDA, "device attributes: %s", cudaGetErrorString(e));
   }
   h->d_err = static_cast<int *>(dalloc(h, sizeof(int) * 4, h->base_allocs));
   h->d_out2 = static_cast<double *>(dalloc(h, sizeof(double) * 2, h->base_allocs));
@@ -647,11 +626,7 @@ static lbm_status build_geometry(lbm_t *h) {
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       h->swap_tma = r == CUDA_SUCCESS;
     }
-    if (h->swap_tma && h->nsm == 0) {
-      int nsm = 0;
-      CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-      h->nsm = nsm;
-    }
+
   }
   if (c.variant == LBM_SWAP && !ind) {
     const SwapTiles t = swap_tiles(h);
@@ -1171,10 +1146,6 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
         const LaunchShape L2 = zpair_shape_of(h);
         if (red_blocks) *red_blocks = (int)blocks_of(L2);
         launch_step_kernel(VAR_AA, 4 + (int)(h->steps & 1), p, k, L2);
-      } else if (use_pairs(h)) {
-        const LaunchShape L2 = pair_shape_of(h);
-        if (red_blocks) *red_blocks = (int)blocks_of(L2);
-        launch_step_kernel(VAR_AA, 2 + (int)(h->steps & 1), p, k, L2);
       } else {
         launch_step_kernel(VAR_AA, (int)(h->steps & 1), p, k, L);
       }
@@ -1238,6 +1209,35 @@ lbm_status lbm_step_flux(lbm_t *h, int n, double *mass, double *jx) {
     if (st != LBM_OK) return st;
   }
   return read_out2(h, mass, jx);
+}
+
+lbm_status lbm_solve_permeability(lbm_t *h, int32_t check, double tol, int64_t max_steps, double *permeability,
+                                  double *mass, double *flux, int64_t *steps) {
+  if (!h) return fail(nullptr, LBM_ERR_INVALID_ARG, "handle is NULL");
+  if (check < 2 || (check & 1)) return fail(h, LBM_ERR_INVALID_ARG, "check interval must be even and >= 2");
+  if (!(tol >= 0.0) || max_steps < check) return fail(h, LBM_ERR_INVALID_ARG, "tol >= 0, max_steps >= check");
+  if (!(h->cfg.omega > 0.0)) return fail(h, LBM_ERR_INVALID_ARG, "permeability needs omega > 0");
+  const int64_t cells = (int64_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+  const double nu = (1.0 / h->cfg.omega - 0.5) / 3.0, gx = h->cfg.force[0];
+  double m = 0.0, j = 0.0, prev = 0.0;
+  bool have_prev = false, steady = false;
+  int64_t done = 0;
+  while (done + check <= max_steps) {
+    // the flux of the state this round starts from
+    lbm_status st = lbm_step_flux(h, check, &m, &j);
+    if (st != LBM_OK) return st;
+    done += check;
+    steady = have_prev && std::fabs(j - prev) < tol * std::fabs(j);
+    if (steady) break;
+    prev = j;
+    have_prev = true;
+  }
+  if (permeability) *permeability = gx != 0.0 ? nu * (j / (double)cells) / gx : NAN;
+  if (mass) *mass = m;
+  if (flux) *flux = j;
+  if (steps) *steps = done;
+  if (!steady) return fail(h, LBM_ERR_NOT_CONVERGED, "flux not steady after %lld steps", (long long)done);
+  return LBM_OK;
 }
 
 }  // extern "C"

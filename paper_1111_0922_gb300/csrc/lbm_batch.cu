@@ -21,159 +21,9 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
-#include "lbm_dispatch.cuh"
-#include "lbm_internal.h"
+#include "lbm_batch.cuh"
 
 namespace lbmk {
-
-constexpr int64_t kAlign = 4096;  // segment alignment in slots
-
-struct BatchSlot {
-  double omega, gx, gy, gz;
-  double omega_m;   // antisymmetric rate (TRT); equal to omega for BGK
-  int64_t start;    // first slot of the segment
-  int64_t nodes;    // fluid nodes
-  int64_t steps;    // steps done before the current round
-  int32_t first_work, nwork;
-  int32_t active, pad;
-};
-
-struct BatchParams {
-  void *A;
-  int64_t npad;
-  const int32_t *idx;  // AA: 18 x npad; ET: 9 x npad (packed)
-  const BatchSlot *slots;
-  const int2 *work;    // (slot, first node of the chunk)
-  int nwork;
-  int t;               // step within the round
-  float scale, inv_scale;
-  double *partials;    // 2 per work chunk
-  int folded;          // AA: IDX holds bounce-back slots instead of -1 (capacity < 2^30)
-};
-
-template <class C>
-__device__ __forceinline__ Lattice<C, 0> batch_lattice(const BatchParams &p) {
-  Lattice<C, 0> L;
-  L.p = static_cast<typename C::S *>(p.A);
-  L.npad = p.npad;
-  L.scale = p.scale;
-  L.inv_scale = p.inv_scale;
-  return L;
-}
-
-// AA pattern over all segments: each block takes the parity of its segment.
-template <class C, bool RED, int NPT>
-__global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_aa(BatchParams p) {
-  using T = typename C::T;
-  const auto A = batch_lattice<C>(p);
-  const int2 w = p.work[blockIdx.x];
-  const BatchSlot &sl = p.slots[w.x];
-  const int64_t end = sl.start + sl.nodes;
-  const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const CollK<T> K = make_collk<T>(T(sl.omega), T(sl.omega_m), T(sl.gx), T(sl.gy), T(sl.gz));
-  double m = 0.0, j = 0.0;
-#pragma unroll
-  for (int r = 0; r < NPT; ++r) {
-    const int64_t n64 = (int64_t)w.y + (int64_t)r * blockDim.x + threadIdx.x;
-    if (n64 >= end) continue;
-    const int s = (int)n64;
-    T d[Q];
-    T drho, rjx;
-    if (!odd) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) d[i] = A.ld(i, s);
-      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
-      const int s2 = launder(s);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) A.st(OPP(i), s2, d[i]);
-    } else if (p.folded) {
-      // every IDX entry is a slot: a solid link holds the slot its
-      // bounce-back uses (see k_batch_rebase)
-      d[0] = A.ld(0, s);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) d[i] = A.ld(OPP(i), __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.npad + s));
-      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
-      const int s2 = launder(s);
-      A.st(0, s2, d[0]);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) A.st(i, __ldg(p.idx + (int64_t)(i - 1) * p.npad + s2), d[i]);
-    } else {
-      d[0] = A.ld(0, s);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int src = __ldg(p.idx + (int64_t)(OPP(i) - 1) * p.npad + s);
-        d[i] = src >= 0 ? A.ld(OPP(i), src) : A.ld(i, s);
-      }
-      collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
-      const int s2 = launder(s);
-      A.st(0, s2, d[0]);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int dst = __ldg(p.idx + (int64_t)(i - 1) * p.npad + s2);
-        if (dst >= 0)
-          A.st(i, dst, d[i]);
-        else
-          A.st(OPP(i), s2, d[i]);
-      }
-    }
-    m += 1.0 + (double)drho;
-    j += (double)rjx;
-  }
-  if (RED) block_reduce_store(m, j, p.partials);
-}
-
-// Esoteric twist over all segments: the array map is the identity after an
-// even step count and swaps opposite directions after an odd one.
-template <class C, bool RED, int NPT>
-__global__ void __launch_bounds__(256, C::kMinBlocks) k_batch_et(BatchParams p) {
-  using T = typename C::T;
-  const auto A = batch_lattice<C>(p);
-  const int2 w = p.work[blockIdx.x];
-  const BatchSlot &sl = p.slots[w.x];
-  const int64_t end = sl.start + sl.nodes;
-  const bool odd = ((sl.steps + p.t) & 1) != 0;
-  const CollK<T> K = make_collk<T>(T(sl.omega), T(sl.omega_m), T(sl.gx), T(sl.gy), T(sl.gz));
-  double m = 0.0, j = 0.0;
-#pragma unroll
-  for (int r = 0; r < NPT; ++r) {
-    const int64_t n64 = (int64_t)w.y + (int64_t)r * blockDim.x + threadIdx.x;
-    if (n64 >= end) continue;
-    const int s = (int)n64;
-    uint32_t wd[10];
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) wd[k] = (uint32_t)__ldg(p.idx + (int64_t)(k - 1) * p.npad + s);
-    // array of direction i: i (even step count) or opp(i) (odd)
-    T d[Q];
-    d[0] = A.ld(0, s);
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-      const int i = 2 * k - 1;
-      const int ai = odd ? i + 1 : i, ai1 = odd ? i : i + 1;
-      d[i] = A.ld(ai, s);
-      d[i + 1] = A.ld(ai1, (int)(wd[k] & 0x7fffffffu));
-    }
-    T drho, rjx;
-    collide_stored<C, true>(d, K, p.scale, p.inv_scale, drho, rjx);
-    const int s2 = launder(s);
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) wd[k] = (uint32_t)launder((int)wd[k]);
-    A.st(0, s2, d[0]);
-#pragma unroll
-    for (int k = 1; k <= 9; ++k) {
-      const int i = 2 * k - 1;
-      const int ai = odd ? i + 1 : i, ai1 = odd ? i : i + 1;
-      const int pos = (int)(wd[k] & 0x7fffffffu);
-      const bool lp = pos < end;
-      const bool lm = (wd[k] >> 31) == 0u;
-      A.st(lp ? ai1 : ai, pos, d[i]);
-      A.st(lm ? ai : ai1, s2, d[i + 1]);
-    }
-    m += 1.0 + (double)drho;
-    j += (double)rjx;
-  }
-  if (RED) block_reduce_store(m, j, p.partials);
-}
 
 // Per-segment sums of its chunk partials, in chunk order (one thread each).
 __global__ void k_batch_slot_sums(const BatchSlot *slots, int nslots, const double *partials, double *out) {
@@ -216,36 +66,15 @@ __global__ void k_batch_rebase(const int32_t *src, int64_t ipad, int rows, int64
   }
 }
 
-template <class C, bool RED, int NPT>
-static void launch_batch_step_t(int variant, const BatchParams &p, int bs, cudaStream_t s) {
-  if (variant == LBM_ET)
-    k_batch_et<C, RED, NPT><<<p.nwork, bs, 0, s>>>(p);
-  else
-    k_batch_aa<C, RED, NPT><<<p.nwork, bs, 0, s>>>(p);
-}
-
-template <class C, bool RED>
-static void launch_batch_npt(int variant, int npt, const BatchParams &p, int bs, cudaStream_t s) {
-  switch (npt) {
-    case 1: launch_batch_step_t<C, RED, 1>(variant, p, bs, s); break;
-    case 2: launch_batch_step_t<C, RED, 2>(variant, p, bs, s); break;
-    case 4: launch_batch_step_t<C, RED, 4>(variant, p, bs, s); break;
-    default: launch_batch_step_t<C, RED, 8>(variant, p, bs, s); break;
-  }
-}
-
-static void launch_batch_step(int precision, int variant, int npt, bool red, const BatchParams &p, int bs,
-                              cudaStream_t s) {
-  if (precision == LBM_F64) {
-    if (red) launch_batch_npt<CodecF64, true>(variant, npt, p, bs, s);
-    else launch_batch_npt<CodecF64, false>(variant, npt, p, bs, s);
-  } else if (precision == LBM_F32) {
-    if (red) launch_batch_npt<CodecF32, true>(variant, npt, p, bs, s);
-    else launch_batch_npt<CodecF32, false>(variant, npt, p, bs, s);
-  } else {
-    if (red) launch_batch_npt<CodecF16S, true>(variant, npt, p, bs, s);
-    else launch_batch_npt<CodecF16S, false>(variant, npt, p, bs, s);
-  }
+// mode 0: one step (p.t), reducing when red; mode 1: k steps in one
+// persistent launch (step 0 reduces).
+static cudaError_t launch_batch(int precision, int variant, int mode, int npt, bool red, const BatchParams &p, int bs,
+                                int k, unsigned *count, int *err, uint64_t limit_ns, int nsm, cudaStream_t s) {
+  if (precision == LBM_F64)
+    return launch_batch_t<CodecF64>(variant, mode, npt, red, p, bs, k, count, err, limit_ns, nsm, s);
+  if (precision == LBM_F32)
+    return launch_batch_t<CodecF32>(variant, mode, npt, red, p, bs, k, count, err, limit_ns, nsm, s);
+  return launch_batch_t<CodecF16S>(variant, mode, npt, red, p, bs, k, count, err, limit_ns, nsm, s);
 }
 
 // Natural state of one AA-pattern segment (even step count) or ET segment.
@@ -273,6 +102,26 @@ __global__ void k_batch_get(BatchParams p, int slot, int variant, double *f_nat)
 using namespace lbmk;
 
 // ---------------------------------------------------------------------------
+// Host record of an admitted geometry: its description (kept so that the
+// autotuner can rebuild the segment for another variant) and the state of
+// its steady-flux test.
+struct SlotHost {
+  int32_t dims[3] = {0, 0, 0}, periodic[3] = {0, 0, 0};
+  std::vector<uint8_t> mask;      // mask admission: nx*ny*nz bytes, nonzero = solid
+  std::vector<int64_t> centres;   // sphere admission: nsph x 3
+  int64_t radius = 0, unit = 1;
+  bool spheres = false;
+  int64_t cells = 0;              // nx*ny*nz
+  int64_t reserved = 0;           // slots of the segment (nodes, ghosts, alignment)
+  double tol = 0.0;               // relative flux change that counts as steady
+  int64_t max_steps = 0;          // step cap (<= 0: none)
+  double mass = 0.0, flux = 0.0;  // of the state the last settled round started from
+  double prev_flux = 0.0;
+  bool have_prev = false;
+  int32_t done = 0;               // 0 running, 1 converged, 2 stopped at max_steps
+  int64_t first_round = 0;        // first round whose results belong to this geometry
+};
+
 struct lbm_batch {
   lbm_batch_config cfg{};
   cudaStream_t stream = nullptr;
@@ -285,7 +134,7 @@ struct lbm_batch {
   std::vector<std::pair<void *, size_t>> allocs;
   // host slot table and free list of [start, end) ranges
   std::vector<BatchSlot> slots;
-  std::vector<int64_t> cells, ghosts;
+  std::vector<SlotHost> host;              // per slot: geometry, convergence record
   std::map<int64_t, int64_t> free_ranges;  // start -> end
   BatchSlot *d_slots = nullptr;
   BatchSlot *h_slots = nullptr;  // pinned mirror
@@ -299,9 +148,25 @@ struct lbm_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_k = -1, graph_nwork = -1, graph_bs = -1, graph_npt = -1;
   bool round_pending = false;
+  int64_t rounds_launched = 0;  // rounds enqueued so far
+  int64_t rounds_settled = 0;   // rounds whose results are folded into the records
+  cudaStream_t admit_stream = nullptr;  // geometry builds, overlapping a round in flight
+  cudaEvent_t admit_done = nullptr;     // the next round waits for the last admission
+  bool admit_pending = false;
   int block_size = 256, npt = 1;
+  int variant = LBM_AA;  // current variant (the tuner may switch it)
+  int round_mode = 0;    // 0 per-step launches, 1 one persistent launch per round
+  int graph_mode = -1;
+  int nsm = 1;
+  unsigned *d_count = nullptr;  // grid barrier of the persistent round
+  int *d_err = nullptr, *h_err = nullptr;  // its timeout flag (pinned copy)
   float scale = 1.0f;
 };
+
+// A persistent round's grid barrier gives up after this long (a round
+// step takes milliseconds; the wait exists to turn a lost block into an
+// error instead of a hang).
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;
 
 static std::string g_batch_error;
 
@@ -353,6 +218,7 @@ extern "C" {
 const char *lbm_batch_last_error(const lbm_batch_t *b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
 
 int64_t lbm_batch_bytes_per_slot(int32_t variant, int32_t precision) {
+  // a batch whose variant may be tuned sizes its index for LBM_AA
   return (int64_t)Q * (int64_t)pdf_bytes(precision) + 4 * (int64_t)idx_rows(variant);
 }
 
@@ -361,6 +227,7 @@ lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out) {
   *out = nullptr;
   if (cfg->variant != LBM_AA && cfg->variant != LBM_ET)
     return bfail(nullptr, LBM_ERR_UNSUPPORTED, "batches run the AA pattern or the esoteric twist");
+  if (cfg->round_mode != 0 && cfg->round_mode != 1) return bfail(nullptr, LBM_ERR_INVALID_ARG, "round_mode");
   if (cfg->precision < LBM_F64 || cfg->precision > LBM_F16S) return bfail(nullptr, LBM_ERR_INVALID_ARG, "precision");
   if (cfg->capacity_slots < kAlign || cfg->capacity_slots >= ((int64_t)1 << 31) - kAlign)
     return bfail(nullptr, LBM_ERR_INVALID_ARG, "capacity_slots must be in [4096, 2^31 - 8192)");
@@ -373,17 +240,22 @@ lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out) {
   b->cfg = *cfg;
   b->stream = static_cast<cudaStream_t>(cfg->stream);
   b->capacity = (cfg->capacity_slots + kAlign - 1) / kAlign * kAlign;
+  b->variant = cfg->variant;
+  b->round_mode = cfg->round_mode;
   b->folded = cfg->variant == LBM_AA && cfg->keep_idx == 0 && b->capacity < ((int64_t)1 << 30);
   b->scale = cfg->precision == LBM_F16S ? (float)cfg->f16_scale : 1.0f;
   b->block_size = cfg->block_size > 0 ? cfg->block_size : 256;
   b->npt = cfg->nodes_per_thread > 0 ? cfg->nodes_per_thread : 1;
-  if (b->block_size % 32 || b->block_size > 256 || kAlign % (b->block_size * b->npt) ||
-      (b->npt != 1 && b->npt != 2 && b->npt != 4 && b->npt != 8)) {
+  if ((b->block_size != 64 && b->block_size != 128 && b->block_size != 256 && b->block_size != 512) ||
+      kAlign % (b->block_size * b->npt) || (b->npt != 1 && b->npt != 2 && b->npt != 4 && b->npt != 8)) {
     delete b;
-    return bfail(nullptr, LBM_ERR_INVALID_ARG, "block_size (<= 256) x nodes_per_thread (1,2,4,8) must divide 4096");
+    return bfail(nullptr, LBM_ERR_INVALID_ARG, "block_size (64..512) x nodes_per_thread (1,2,4,8) must divide 4096");
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
   b->state_bytes = (size_t)Q * b->capacity * pdf_bytes(cfg->precision);
-  b->idx_bytes = (size_t)idx_rows(cfg->variant) * b->capacity * 4;
+  b->idx_bytes = (size_t)(cfg->tune_variant ? 18 : idx_rows(cfg->variant)) * b->capacity * 4;
   b->slot_capacity = cfg->max_geometries;
   b->work_capacity = (int)(b->capacity / 32) + cfg->max_geometries;
   b->d_A = balloc(b, b->state_bytes, true);
@@ -392,9 +264,16 @@ lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out) {
   b->d_work = static_cast<int2 *>(balloc(b, sizeof(int2) * b->work_capacity, true));
   b->d_partials = static_cast<double *>(balloc(b, sizeof(double) * 2 * b->work_capacity, true));
   b->d_sums = static_cast<double *>(balloc(b, sizeof(double) * 2 * b->slot_capacity, true));
-  bool ok = b->d_A && b->d_idx && b->d_slots && b->d_work && b->d_partials && b->d_sums;
+  b->d_count = static_cast<unsigned *>(balloc(b, 256, true));
+  b->d_err = static_cast<int *>(balloc(b, 256, true));
+  bool ok = b->d_A && b->d_idx && b->d_slots && b->d_work && b->d_partials && b->d_sums && b->d_count && b->d_err;
+  ok = ok && cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->h_err, sizeof(int)) == cudaSuccess;
+  if (ok) *b->h_err = 0;
   ok = ok && cudaMallocHost(&b->h_sums, sizeof(double) * 2 * b->slot_capacity) == cudaSuccess;
   ok = ok && cudaMallocHost(&b->h_slots, sizeof(BatchSlot) * b->slot_capacity) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->admit_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->admit_done, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     lbm_batch_destroy(b);
@@ -408,10 +287,14 @@ lbm_status lbm_batch_create(const lbm_batch_config *cfg, lbm_batch_t **out) {
 lbm_status lbm_batch_destroy(lbm_batch_t *b) {
   if (!b) return LBM_OK;
   cudaStreamSynchronize(b->stream);
+  if (b->admit_stream) cudaStreamSynchronize(b->admit_stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->admit_done) cudaEventDestroy(b->admit_done);
+  if (b->admit_stream) cudaStreamDestroy(b->admit_stream);
   for (auto &a : b->allocs) bfree(b, a.first, a.second);
   if (b->h_sums) cudaFreeHost(b->h_sums);
   if (b->h_slots) cudaFreeHost(b->h_slots);
+  if (b->h_err) cudaFreeHost(b->h_err);
   delete b;
   return LBM_OK;
 }
@@ -496,35 +379,59 @@ static BatchParams batch_params(const lbm_batch_t *b) {
   return p;
 }
 
-extern "C" {
-
-lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const int32_t *periodic, int64_t nsph,
-                                   const int64_t *centres, int64_t radius, int64_t unit, double omega,
-                                   const double *force, int32_t *slot_out) {
-  if (!b || !dims || !periodic || !force || !slot_out) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
-  if (b->round_pending) BCUDA(b, cudaStreamSynchronize(b->stream));
-  const int nx = dims[0], ny = dims[1], nz = dims[2];
-  for (int a = 0; a < 3; ++a)
-    if (dims[a] < 1 || (periodic[a] && dims[a] < 2)) return bfail(b, LBM_ERR_INVALID_ARG, "box extents");
-  if (!(omega > 0.0 && omega < 2.0)) return bfail(b, LBM_ERR_INVALID_ARG, "omega");
-  if (nsph < 0 || (nsph > 0 && !centres) || unit < 1 || radius < 0) return bfail(b, LBM_ERR_INVALID_ARG, "spheres");
-  const int64_t ncell = (int64_t)nx * ny * nz;
-  if (ncell >= ((int64_t)1 << 30)) return bfail(b, LBM_ERR_INVALID_ARG, "box too large");
-  // free slot-table entry
-  int slot = -1;
-  for (size_t s = 0; s < b->slots.size(); ++s)
-    if (!b->slots[s].active) {
-      slot = (int)s;
-      break;
+// Fold the results of every completed round into the slot records: the
+// relative flux change between consecutive rounds (each round reduces the
+// state it starts from) decides convergence, as in the single-lattice solve.
+static lbm_status settle(lbm_batch_t *b) {
+  if (b->round_pending) {
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->round_pending = false;
+    if (*b->h_err) {
+      *b->h_err = 0;
+      b->rounds_settled = b->rounds_launched;
+      return bfail(b, LBM_ERR_TIMEOUT, "a persistent round's grid barrier gave up; its results are invalid");
     }
-  if (slot < 0) {
-    if ((int)b->slots.size() >= b->slot_capacity) return bfail(b, LBM_ERR_OOM, "all %d geometry slots in use", b->slot_capacity);
-    slot = (int)b->slots.size();
-    b->slots.push_back(BatchSlot{});
-    b->cells.push_back(0);
-    b->ghosts.push_back(0);
   }
-  // temporaries for the geometry build
+  if (b->rounds_settled == b->rounds_launched) return LBM_OK;
+  for (size_t s = 0; s < b->slots.size(); ++s) {
+    const BatchSlot &sl = b->slots[s];
+    SlotHost &h = b->host[s];
+    if (!sl.active || h.first_round > b->rounds_launched - 1) continue;
+    h.mass = b->h_sums[2 * s];
+    h.flux = b->h_sums[2 * s + 1];
+    if (h.done) continue;
+    const bool steady = h.have_prev && std::fabs(h.flux - h.prev_flux) < h.tol * std::fabs(h.flux);
+    h.prev_flux = h.flux;
+    h.have_prev = true;
+    if (steady)
+      h.done = 1;
+    else if (h.max_steps > 0 && sl.steps >= h.max_steps)
+      h.done = 2;
+  }
+  b->rounds_settled = b->rounds_launched;
+  return LBM_OK;
+}
+
+// Darcy permeability k = nu <rho u_x> / g_x, the average over every cell of
+// the box (superficial velocity), nu = (1/omega - 1/2) / 3 (lattice units).
+static double permeability_of(double flux, int64_t cells, double omega, double gx) {
+  const double nu = (1.0 / omega - 0.5) / 3.0;
+  return gx != 0.0 && cells > 0 ? nu * (flux / (double)cells) / gx : NAN;
+}
+
+// Build geometry `slot` (its host record filled) for the batch's variant:
+// solid mask on the device (uploaded or from spheres), node list, IDX or the
+// esoteric twist's packed index, a free range, the rebased index and the
+// rest state, all on the admission stream (a round in flight touches only
+// the ranges of active geometries, so the two overlap).  Fills sl.start,
+// sl.nodes and host.reserved.
+static lbm_status build_segment(lbm_batch_t *b, int slot) {
+  SlotHost &h = b->host[slot];
+  BatchSlot &sl = b->slots[slot];
+  cudaStream_t st = b->admit_stream;
+  const int nx = h.dims[0], ny = h.dims[1], nz = h.dims[2];
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t nsph = h.spheres ? (int64_t)h.centres.size() / 3 : 0;
   const int64_t ext = (int64_t)(nx + 2) * (ny + 2) * (nz + 2);
   const int64_t sc = scan_scratch_elems(std::max(ncell, ext));
   std::vector<std::pair<void *, size_t>> tmp;
@@ -534,7 +441,7 @@ lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const in
     return p;
   };
   auto cleanup = [&]() {
-    cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(st);
     for (auto &a : tmp) bfree(b, a.first, a.second);
     tmp.clear();
   };
@@ -547,34 +454,38 @@ lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const in
     cleanup();
     return bfail(b, LBM_ERR_OOM, "geometry temporaries");
   }
-  cudaMemsetAsync(solid, 0, ncell, b->stream);
-  if (nsph > 0) {
-    cudaMemcpyAsync(dcen, centres, sizeof(int64_t) * 3 * nsph, cudaMemcpyHostToDevice, b->stream);
-    launch_sphere_mask(solid, nx, ny, nz, periodic, nsph, dcen, radius, unit, b->stream);
+  if (h.spheres) {
+    cudaMemsetAsync(solid, 0, ncell, st);
+    if (nsph > 0) {
+      cudaMemcpyAsync(dcen, h.centres.data(), sizeof(int64_t) * 3 * nsph, cudaMemcpyHostToDevice, st);
+      launch_sphere_mask(solid, nx, ny, nz, h.periodic, nsph, dcen, h.radius, h.unit, st);
+    }
+  } else {
+    cudaMemcpyAsync(solid, h.mask.data(), ncell, cudaMemcpyHostToDevice, st);
   }
-  const int64_t N = build_node_list(solid, ncell, node_of, cells, scratch, sc, b->stream);
+  const int64_t N = build_node_list(solid, ncell, node_of, cells, scratch, sc, st);
   if (N < 0) {
     cleanup();
     return bfail(b, LBM_ERR_CUDA, "node list");
   }
   const int64_t ipad = std::max<int64_t>(64, (N + 63) / 64 * 64);
-  const int rows = idx_rows(b->cfg.variant);
+  const int rows = idx_rows(b->variant);
   int32_t *idx = static_cast<int32_t *>(talloc(sizeof(int32_t) * 18 * ipad));
   if (!idx) {
     cleanup();
     return bfail(b, LBM_ERR_OOM, "IDX temporaries");
   }
-  launch_build_idx(cells, node_of, N, nx, ny, nz, periodic, idx, ipad, b->stream);
+  launch_build_idx(cells, node_of, N, nx, ny, nz, h.periodic, idx, ipad, st);
   int64_t G = 0;
   int32_t *src_idx = idx;
-  if (b->cfg.variant == LBM_ET) {
+  if (b->variant == LBM_ET) {
     int32_t *ghost = static_cast<int32_t *>(talloc(sizeof(int32_t) * ext));
     int32_t *et = static_cast<int32_t *>(talloc(sizeof(int32_t) * 9 * ipad));
     if (!ghost || !et) {
       cleanup();
       return bfail(b, LBM_ERR_OOM, "ET temporaries");
     }
-    G = build_et_index(cells, node_of, N, nx, ny, nz, periodic, ghost, et, ipad, scratch, sc, b->stream);
+    G = build_et_index(cells, node_of, N, nx, ny, nz, h.periodic, ghost, et, ipad, scratch, sc, st);
     src_idx = et;
   }
   const int64_t len = std::max<int64_t>(kAlign, (N + G + kAlign - 1) / kAlign * kAlign);
@@ -585,48 +496,123 @@ lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const in
                  (long long)N);
   }
   if (N > 0)
-    k_batch_rebase<<<(unsigned)std::min<int64_t>((rows * N + 255) / 256, 1 << 20), 256, 0, b->stream>>>(
-        src_idx, ipad, rows, N, b->d_idx, b->capacity, start, b->cfg.variant == LBM_ET, b->folded ? 1 : 0);
+    k_batch_rebase<<<(unsigned)std::min<int64_t>((rows * N + 255) / 256, 1 << 20), 256, 0, st>>>(
+        src_idx, ipad, rows, N, b->d_idx, b->capacity, start, b->variant == LBM_ET, b->folded ? 1 : 0);
   // rest state: every deviation zero, the segment's ghosts included
   const size_t es = pdf_bytes(b->cfg.precision);
   for (int i = 0; i < Q; ++i)
-    cudaMemsetAsync(static_cast<char *>(b->d_A) + ((int64_t)i * b->capacity + start) * es, 0, len * es, b->stream);
-  cudaError_t e = cudaGetLastError();
+    cudaMemsetAsync(static_cast<char *>(b->d_A) + ((int64_t)i * b->capacity + start) * es, 0, len * es, st);
+  cudaError_t e = cudaEventRecord(b->admit_done, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
   cleanup();
   if (e != cudaSuccess) {
     give_range(b, start, len);
     return bfail(b, LBM_ERR_CUDA, "admission kernels: %s", cudaGetErrorString(e));
   }
+  b->admit_pending = true;
+  sl.start = start;
+  sl.nodes = N;
+  h.reserved = len;
+  return LBM_OK;
+}
+
+// Admission common to masks and sphere packs: validate, take a table entry,
+// build the segment, set the slot's parameters (at rest, step 0).
+static lbm_status admit(lbm_batch_t *b, SlotHost &&h, double omega, const double *force, int32_t *slot_out) {
+  for (int a = 0; a < 3; ++a)
+    if (h.dims[a] < 1 || (h.periodic[a] && h.dims[a] < 2)) return bfail(b, LBM_ERR_INVALID_ARG, "box extents");
+  if (!(omega > 0.0 && omega < 2.0)) return bfail(b, LBM_ERR_INVALID_ARG, "omega");
+  if (!(h.tol >= 0.0)) return bfail(b, LBM_ERR_INVALID_ARG, "tol must be >= 0");
+  h.cells = (int64_t)h.dims[0] * h.dims[1] * h.dims[2];
+  if (h.cells >= ((int64_t)1 << 30)) return bfail(b, LBM_ERR_INVALID_ARG, "box too large");
+  // a release or the previous admission may still be pending on the host side
+  int slot = -1;
+  for (size_t s = 0; s < b->slots.size(); ++s)
+    if (!b->slots[s].active) {
+      slot = (int)s;
+      break;
+    }
+  if (slot < 0) {
+    if ((int)b->slots.size() >= b->slot_capacity) return bfail(b, LBM_ERR_OOM, "all %d geometry slots in use", b->slot_capacity);
+    slot = (int)b->slots.size();
+    b->slots.push_back(BatchSlot{});
+    b->host.push_back(SlotHost{});
+  }
+  b->host[slot] = std::move(h);
   BatchSlot &sl = b->slots[slot];
   memset(&sl, 0, sizeof sl);
+  lbm_status st = build_segment(b, slot);
+  if (st != LBM_OK) return st;
   sl.omega = omega;
   sl.omega_m = omega;
   sl.gx = force[0];
   sl.gy = force[1];
   sl.gz = force[2];
-  sl.start = start;
-  sl.nodes = N;
   sl.steps = 0;
   sl.active = 1;
-  b->cells[slot] = ncell;
-  b->ghosts[slot] = len;  // reserved length
+  // results of the round in flight (if any) do not belong to this geometry
+  b->host[slot].first_round = b->rounds_launched;
   b->dirty = true;
   *slot_out = slot;
   return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_batch_admit(lbm_batch_t *b, const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
+                           const int32_t *periodic, double omega, const double *force, double tol, int64_t max_steps,
+                           int32_t *slot_out) {
+  if (!b || !mask || !periodic || !force || !slot_out) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= ((int64_t)1 << 30))
+    return bfail(b, LBM_ERR_INVALID_ARG, "box extents");
+  SlotHost h;
+  h.dims[0] = nx;
+  h.dims[1] = ny;
+  h.dims[2] = nz;
+  for (int a = 0; a < 3; ++a) h.periodic[a] = periodic[a] ? 1 : 0;
+  h.mask.assign(mask, mask + (int64_t)nx * ny * nz);
+  h.tol = tol;
+  h.max_steps = max_steps;
+  return admit(b, std::move(h), omega, force, slot_out);
+}
+
+lbm_status lbm_batch_admit_spheres(lbm_batch_t *b, const int32_t *dims, const int32_t *periodic, int64_t nsph,
+                                   const int64_t *centres, int64_t radius, int64_t unit, double omega,
+                                   const double *force, double tol, int64_t max_steps, int32_t *slot_out) {
+  if (!b || !dims || !periodic || !force || !slot_out) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
+  if (nsph < 0 || (nsph > 0 && !centres) || unit < 1 || radius < 0) return bfail(b, LBM_ERR_INVALID_ARG, "spheres");
+  SlotHost h;
+  for (int a = 0; a < 3; ++a) {
+    h.dims[a] = dims[a];
+    h.periodic[a] = periodic[a] ? 1 : 0;
+  }
+  h.spheres = true;
+  if (nsph > 0) h.centres.assign(centres, centres + 3 * nsph);
+  h.radius = radius;
+  h.unit = unit;
+  h.tol = tol;
+  h.max_steps = max_steps;
+  return admit(b, std::move(h), omega, force, slot_out);
 }
 
 lbm_status lbm_batch_release(lbm_batch_t *b, int32_t slot) {
   if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL batch");
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
     return bfail(b, LBM_ERR_INVALID_ARG, "slot %d is not in use", slot);
-  if (b->round_pending) BCUDA(b, cudaStreamSynchronize(b->stream));
-  give_range(b, b->slots[slot].start, b->ghosts[slot]);
+  // the range may be in use by a round in flight: finish it first
+  lbm_status st = settle(b);
+  if (st != LBM_OK) return st;
+  give_range(b, b->slots[slot].start, b->host[slot].reserved);
   b->slots[slot].active = 0;
+  b->host[slot] = SlotHost{};
   b->dirty = true;
   return LBM_OK;
 }
 
-// Capture K steps (the first reducing) and the per-slot sums into a graph.
+// Capture a round into a graph: K steps (the first reducing) as K launches
+// (round_mode 0) or one persistent cooperative launch (round_mode 1), the
+// per-slot sums and their copy (with the barrier's timeout flag) to pinned
+// host memory.
 static lbm_status capture_round(lbm_batch_t *b, int k) {
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
@@ -635,37 +621,57 @@ static lbm_status capture_round(lbm_batch_t *b, int k) {
   cudaStream_t cs;
   BCUDA(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
+  cudaError_t le = cudaSuccess;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     BatchParams p = batch_params(b);
-    for (int t = 0; t < k; ++t) {
-      p.t = t;
-      launch_batch_step(b->cfg.precision, b->cfg.variant, b->npt, t == 0, p, b->block_size, cs);
-      if (t == 0)
-        k_batch_slot_sums<<<((int)b->slots.size() + 127) / 128, 128, 0, cs>>>(b->d_slots, (int)b->slots.size(),
-                                                                                b->d_partials, b->d_sums);
+    const int nslots = (int)b->slots.size();
+    if (b->round_mode == 1) {
+      cudaMemsetAsync(b->d_count, 0, sizeof(unsigned), cs);
+      cudaMemsetAsync(b->d_err, 0, sizeof(int), cs);
+      le = launch_batch(b->cfg.precision, b->variant, 1, b->npt, true, p, b->block_size, k, b->d_count, b->d_err,
+                        kBarrierLimitNs, b->nsm, cs);
+      k_batch_slot_sums<<<(nslots + 127) / 128, 128, 0, cs>>>(b->d_slots, nslots, b->d_partials, b->d_sums);
+    } else {
+      for (int t = 0; t < k && le == cudaSuccess; ++t) {
+        p.t = t;
+        le = launch_batch(b->cfg.precision, b->variant, 0, b->npt, t == 0, p, b->block_size, 1, nullptr, nullptr, 0,
+                          b->nsm, cs);
+        if (t == 0)
+          k_batch_slot_sums<<<(nslots + 127) / 128, 128, 0, cs>>>(b->d_slots, nslots, b->d_partials, b->d_sums);
+      }
     }
-    cudaMemcpyAsync(b->h_sums, b->d_sums, sizeof(double) * 2 * b->slots.size(), cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(b->h_sums, b->d_sums, sizeof(double) * 2 * nslots, cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, cs);
     e = cudaStreamEndCapture(cs, &g);
-  }
-  if (e == cudaSuccess) {
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
+    if (le != cudaSuccess && e == cudaSuccess) {
+      cudaGraphDestroy(g);
+      e = le;
+    } else if (e == cudaSuccess) {
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+    }
   }
   cudaStreamDestroy(cs);
-  if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "round graph: %s", cudaGetErrorString(e));
+  cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "round graph (mode %d): %s", b->round_mode, cudaGetErrorString(e));
   b->graph_k = k;
   b->graph_nwork = b->nwork;
   b->graph_bs = b->block_size;
   b->graph_npt = b->npt;
+  b->graph_mode = b->round_mode;
   return LBM_OK;
 }
 
 lbm_status lbm_batch_round(lbm_batch_t *b, int32_t k) {
   if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL batch");
   if (k < 1) return bfail(b, LBM_ERR_INVALID_ARG, "k_steps must be >= 1");
-  if (b->round_pending) BCUDA(b, cudaStreamSynchronize(b->stream));
-  b->round_pending = false;
+  lbm_status st0 = settle(b);
+  if (st0 != LBM_OK) return st0;
+  if (b->admit_pending) {  // segments built on the admission stream
+    BCUDA(b, cudaStreamWaitEvent(b->stream, b->admit_done, 0));
+    b->admit_pending = false;
+  }
   bool rebuilt = false;
   if (b->dirty) {
     lbm_status st = rebuild_work(b);
@@ -676,7 +682,7 @@ lbm_status lbm_batch_round(lbm_batch_t *b, int32_t k) {
   if (st != LBM_OK) return st;
   if (b->nwork == 0) return LBM_OK;
   if (!b->graph || rebuilt || b->graph_k != k || b->graph_nwork != b->nwork || b->graph_bs != b->block_size ||
-      b->graph_npt != b->npt) {
+      b->graph_npt != b->npt || b->graph_mode != b->round_mode) {
     st = capture_round(b, k);
     if (st != LBM_OK) return st;
   }
@@ -684,20 +690,33 @@ lbm_status lbm_batch_round(lbm_batch_t *b, int32_t k) {
   for (auto &sl : b->slots)
     if (sl.active) sl.steps += k;
   b->round_pending = true;
+  b->rounds_launched += 1;
   return LBM_OK;
 }
 
-lbm_status lbm_batch_poll(lbm_batch_t *b, int32_t slot, double *mass, double *flux, int64_t *steps) {
+lbm_status lbm_batch_flux(lbm_batch_t *b, int32_t slot, double *mass, double *flux, int64_t *steps) {
   if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL batch");
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
     return bfail(b, LBM_ERR_INVALID_ARG, "slot %d is not in use", slot);
-  if (b->round_pending) {
-    BCUDA(b, cudaStreamSynchronize(b->stream));
-    b->round_pending = false;
-  }
-  if (mass) *mass = b->h_sums[2 * slot];
-  if (flux) *flux = b->h_sums[2 * slot + 1];
+  lbm_status st = settle(b);
+  if (st != LBM_OK) return st;
+  if (mass) *mass = b->host[slot].mass;
+  if (flux) *flux = b->host[slot].flux;
   if (steps) *steps = b->slots[slot].steps;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_poll(lbm_batch_t *b, int32_t slot, int32_t *done, double *permeability, int64_t *steps) {
+  if (!b) return bfail(nullptr, LBM_ERR_INVALID_ARG, "NULL batch");
+  if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
+    return bfail(b, LBM_ERR_INVALID_ARG, "slot %d is not in use", slot);
+  lbm_status st = settle(b);
+  if (st != LBM_OK) return st;
+  const BatchSlot &sl = b->slots[slot];
+  const SlotHost &h = b->host[slot];
+  if (done) *done = h.done;
+  if (permeability) *permeability = permeability_of(h.flux, h.cells, sl.omega, sl.gx);
+  if (steps) *steps = sl.steps;
   return LBM_OK;
 }
 
@@ -706,7 +725,7 @@ lbm_status lbm_batch_slot_info(lbm_batch_t *b, int32_t slot, int64_t *nodes, int
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
     return bfail(b, LBM_ERR_INVALID_ARG, "slot %d is not in use", slot);
   if (nodes) *nodes = b->slots[slot].nodes;
-  if (cells) *cells = b->cells[slot];
+  if (cells) *cells = b->host[slot].cells;
   if (steps) *steps = b->slots[slot].steps;
   return LBM_OK;
 }
@@ -731,6 +750,8 @@ lbm_status lbm_batch_get_info(lbm_batch_t *b, lbm_batch_info *info) {
   info->block_size = b->block_size;
   info->nodes_per_thread = b->npt;
   info->work_chunks = b->nwork;
+  info->variant = b->variant;
+  info->round_mode = b->round_mode;
   return LBM_OK;
 }
 
@@ -739,11 +760,15 @@ lbm_status lbm_batch_get_pdfs(lbm_batch_t *b, int32_t slot, double *f_host) {
   if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].active)
     return bfail(b, LBM_ERR_INVALID_ARG, "slot %d is not in use", slot);
   const BatchSlot sl = b->slots[slot];
-  if (b->cfg.variant == LBM_AA && (sl.steps & 1))
+  if (b->variant == LBM_AA && (sl.steps & 1))
     return bfail(b, LBM_ERR_STATE, "AA pattern state is natural only after an even step count");
-  if (b->round_pending) BCUDA(b, cudaStreamSynchronize(b->stream));
-  b->round_pending = false;
-  lbm_status st = upload_slots(b);
+  lbm_status st = settle(b);
+  if (st != LBM_OK) return st;
+  if (b->admit_pending) {
+    BCUDA(b, cudaStreamWaitEvent(b->stream, b->admit_done, 0));
+    b->admit_pending = false;
+  }
+  st = upload_slots(b);
   if (st != LBM_OK) return st;
   const size_t bytes = sizeof(double) * Q * std::max<int64_t>(sl.nodes, 1);
   double *tmp = static_cast<double *>(balloc(b, bytes, false));
@@ -751,11 +776,11 @@ lbm_status lbm_batch_get_pdfs(lbm_batch_t *b, int32_t slot, double *f_host) {
   BatchParams p = batch_params(b);
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((sl.nodes + 255) / 256, 1 << 20));
   if (b->cfg.precision == LBM_F64)
-    k_batch_get<CodecF64><<<grid, 256, 0, b->stream>>>(p, slot, b->cfg.variant, tmp);
+    k_batch_get<CodecF64><<<grid, 256, 0, b->stream>>>(p, slot, b->variant, tmp);
   else if (b->cfg.precision == LBM_F32)
-    k_batch_get<CodecF32><<<grid, 256, 0, b->stream>>>(p, slot, b->cfg.variant, tmp);
+    k_batch_get<CodecF32><<<grid, 256, 0, b->stream>>>(p, slot, b->variant, tmp);
   else
-    k_batch_get<CodecF16S><<<grid, 256, 0, b->stream>>>(p, slot, b->cfg.variant, tmp);
+    k_batch_get<CodecF16S><<<grid, 256, 0, b->stream>>>(p, slot, b->variant, tmp);
   cudaError_t e = cudaMemcpyAsync(f_host, tmp, sizeof(double) * Q * sl.nodes, cudaMemcpyDeviceToHost, b->stream);
   cudaError_t e2 = cudaStreamSynchronize(b->stream);
   bfree(b, tmp, bytes);
@@ -763,54 +788,117 @@ lbm_status lbm_batch_get_pdfs(lbm_batch_t *b, int32_t slot, double *f_host) {
   return LBM_OK;
 }
 
-// Launch-shape autotuner: time `rounds` rounds of k steps of the current
-// batch for each (block size, nodes per thread) candidate with CUDA events,
-// keep the fastest.  The state advances by rounds * k steps per candidate.
-lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *best_bs, int32_t *best_npt,
-                          double *best_mflups) {
+}  // extern "C"
+
+// Rebuild every active geometry for `variant` (index data and, for the
+// esoteric twist, ghost slots), laid out again from the start of the arrays,
+// at rest.  On failure the previous variant is restored the same way.
+static lbm_status relayout(lbm_batch_t *b, int variant) {
+  lbm_status st = settle(b);
+  if (st != LBM_OK) return st;
+  BCUDA(b, cudaStreamSynchronize(b->admit_stream));
+  const int old = b->variant;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const int v = attempt == 0 ? variant : old;
+    b->variant = v;
+    b->folded = v == LBM_AA && b->cfg.keep_idx == 0 && b->capacity < ((int64_t)1 << 30);
+    b->free_ranges.clear();
+    b->free_ranges[0] = b->capacity;
+    st = LBM_OK;
+    for (size_t s = 0; s < b->slots.size() && st == LBM_OK; ++s) {
+      if (!b->slots[s].active) continue;
+      st = build_segment(b, (int)s);
+      BatchSlot &sl = b->slots[s];
+      SlotHost &h = b->host[s];
+      sl.steps = 0;
+      h.have_prev = false;
+      h.done = 0;
+      h.mass = h.flux = 0.0;
+      h.first_round = b->rounds_launched;
+    }
+    b->dirty = true;
+    if (st == LBM_OK) break;
+    if (attempt == 1) return bfail(b, LBM_ERR_CUDA, "relayout to the previous variant failed");
+  }
+  BCUDA(b, cudaStreamSynchronize(b->admit_stream));
+  b->admit_pending = false;
+  return b->variant == variant ? LBM_OK : bfail(b, LBM_ERR_OOM, "the geometries do not fit in variant %d", variant);
+}
+
+extern "C" {
+
+// Autotuner: for each candidate (variant, block size, nodes per thread,
+// round mode) one warm-up round (graph capture) and `rounds` rounds of k
+// steps timed with CUDA events; the fastest is kept and every geometry
+// restarts from rest in it.
+lbm_status lbm_batch_tune(lbm_batch_t *b, int32_t rounds, int32_t k, int32_t *best_variant, int32_t *best_bs,
+                          int32_t *best_npt, int32_t *best_mode, double *best_mflups) {
   if (!b || rounds < 1 || k < 1) return bfail(b, LBM_ERR_INVALID_ARG, "tune arguments");
-  static const int cand[][2] = {{128, 1}, {256, 1}, {128, 2}, {256, 2}, {128, 4}, {256, 4}, {64, 2}, {64, 4}};
   int64_t active = 0;
   for (auto &sl : b->slots)
     if (sl.active) active += sl.nodes;
   if (active == 0) return bfail(b, LBM_ERR_STATE, "no active geometry to tune on");
+  std::vector<int> variants{b->variant};
+  if (b->cfg.tune_variant) variants = {LBM_AA, LBM_ET};
+  static const int sizes[] = {128, 256, 512};
+  static const int npts[] = {1, 2, 4, 8};
   double best = -1.0;
-  int bb = b->block_size, bn = b->npt;
+  int bv = b->variant, bb = b->block_size, bn = b->npt, bm = b->round_mode;
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
-  for (auto &c : cand) {
-    b->block_size = c[0];
-    b->npt = c[1];
-    b->dirty = true;
-    lbm_status st = lbm_batch_round(b, k);  // warm-up and graph capture
-    if (st != LBM_OK) return st;
-    BCUDA(b, cudaStreamSynchronize(b->stream));
-    b->round_pending = false;
-    cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < rounds; ++r) {
-      st = lbm_batch_round(b, k);
-      if (st != LBM_OK) return st;
-    }
-    cudaEventRecord(e1, b->stream);
-    BCUDA(b, cudaEventSynchronize(e1));
-    b->round_pending = false;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const double mflups = (double)active * rounds * k / (ms * 1e-3) / 1e6;
-    if (mflups > best) {
-      best = mflups;
-      bb = c[0];
-      bn = c[1];
-    }
+  lbm_status result = LBM_OK;
+  for (int v : variants) {
+    if (v != b->variant && relayout(b, v) != LBM_OK) continue;  // does not fit: skip the variant
+    for (int bs : sizes)
+      for (int npt : npts)
+        for (int mode = 0; mode < 2; ++mode) {
+          if (kAlign % (bs * npt)) continue;
+          b->block_size = bs;
+          b->npt = npt;
+          b->round_mode = mode;
+          b->dirty = true;
+          lbm_status st = lbm_batch_round(b, k);  // warm-up and graph capture
+          if (st == LBM_OK) st = settle(b);
+          if (st != LBM_OK) {
+            if (mode == 1 && st == LBM_ERR_CUDA) continue;  // no co-resident grid for this shape
+            result = st;
+            goto done;
+          }
+          cudaEventRecord(e0, b->stream);
+          for (int r = 0; r < rounds && st == LBM_OK; ++r) st = lbm_batch_round(b, k);
+          cudaEventRecord(e1, b->stream);
+          if (st == LBM_OK) st = settle(b);
+          if (st != LBM_OK) {
+            result = st;
+            goto done;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          const double mflups = (double)active * rounds * k / (ms * 1e-3) / 1e6;
+          if (mflups > best) {
+            best = mflups;
+            bv = v;
+            bb = bs;
+            bn = npt;
+            bm = mode;
+          }
+        }
   }
+done:
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (result != LBM_OK) return result;
+  if (best < 0) return bfail(b, LBM_ERR_CUDA, "no candidate ran");
   b->block_size = bb;
   b->npt = bn;
-  b->dirty = true;
+  b->round_mode = bm;
+  lbm_status st = relayout(b, bv);  // every geometry back to rest in the chosen variant
+  if (st != LBM_OK) return st;
+  if (best_variant) *best_variant = bv;
   if (best_bs) *best_bs = bb;
   if (best_npt) *best_npt = bn;
+  if (best_mode) *best_mode = bm;
   if (best_mflups) *best_mflups = best;
   return LBM_OK;
 }

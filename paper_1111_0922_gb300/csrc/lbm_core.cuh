@@ -184,14 +184,17 @@ __device__ __forceinline__ int64_t grid_position(const Grid &g, int x, int y, in
 //     d*_i = a* + b*,  d*_opp = a* - b*
 //   rest: d*_0 = d_0 - lp (d_0 - w_0 [(rho - 1) - 1.5 rho u.u]) - (1 - lp/2) w_0 rho 3 u.g
 //
-// Evaluated with the terms regrouped so that each pair costs about ten
-// operations: with A = lp (rho - 1) - rho (1.5 lp u.u + 3 (1 - lp/2) u.g),
+// Evaluated with the terms regrouped so that each opposite pair costs six to
+// ten operations, with A = lp (rho - 1) - rho (1.5 lp u.u + 3 (1 - lp/2) u.g):
 //   a* = (1 - lp)/2 (d_i + d_opp) + w_i A + rho (c.u) (4.5 lp w_i c.u + 9 (1 - lp/2) w_i c.g)
 //   b* = (1 - lm)/2 (d_i - d_opp) + rho (3 lm w_i c.u + 3 (1 - lm/2) w_i c.g)
 //   d*_0 = (1 - lp) d_0 + w_0 A
-// and for BGK d*_i = (1 - lp) d_i + (P +- M) with P +- M formed in one
-// chain per member (below), which keeps lp = 0 (no collision) an exact
-// identity.
+// collide_f32 forms u; collide_f64 never does: with J = rho u and sc = c.J,
+// rho u.u = J.J / rho, rho u.g = J.g and rho (c.u)^2 = sc^2 / rho, so one
+// reciprocal of rho serves every pair and c.J costs additions alone; its
+// moments come from direction-group sums.  For BGK d*_i = (1 - lp) d_i +
+// (P +- M) with P +- M formed in one chain per member (below), which keeps
+// lp = 0 (no collision) an exact identity.
 //
 // With SCALED the d_i arrive multiplied by the storage scale s (a power of
 // two, S for F16S) and leave multiplied by it; the moments are unscaled
@@ -245,6 +248,7 @@ struct CollK {
   T zp[10], zm[10];  // fp_k + tm_c, fp_k - tm_c (c the weight class of pair k)
   T hg[3], g[3];     // g/2, g
   int bgk;           // lm == lp
+  int gx_only;       // g = (gx, 0, 0): the FP64 collision drops the zero force terms
 };
 
 template <typename T>
@@ -279,20 +283,42 @@ __host__ __device__ inline CollK<T> make_collk(T lp, T lm, T gx, T gy, T gz) {
   K.g[2] = gz;
   for (int a = 0; a < 3; ++a) K.hg[a] = R::mul(T(0.5), K.g[a]);
   K.bgk = lm == lp;
+  K.gx_only = gy == T(0) && gz == T(0);
   return K;
 }
 
 template <typename T>
-__device__ __forceinline__ T recip(T x) {
-  return T(1) / x;
-}
+__device__ __forceinline__ T recip(T x);
 template <>
 __device__ __forceinline__ float recip<float>(float x) {
   return __fdividef(1.0f, x);  // rho is near 1: the fast reciprocal is well within FP32 parity
 }
+// FP64: Newton-Raphson iteration for 1/x (Newton's method on g(r) = 1/r - x:
+// r <- r + r (1 - x r), which squares the relative error of r), started from
+// the hardware's approximate reciprocal (rcp.approx.ftz.f64, accurate to
+// about 20 bits; two steps take the error below 2^-70 before the final
+// rounding, so the result is within one unit in the last place of 1/x).
+// Four FMAs instead of the correctly rounded division's longer sequence and
+// range checks: the FP64 pipe bounds every FP64 step kernel on GB300.
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = __fma_rn(-x, r, 1.0);
+  r = __fma_rn(r, e, r);
+  e = __fma_rn(-x, r, 1.0);
+  return __fma_rn(r, e, r);
+}
+
+// Sum of the five d_i with i in {a, b, c, e, f}, as a fixed tree.
+template <typename T>
+__device__ __forceinline__ T sum5(const T (&d)[Q], int a, int b, int c, int e, int f) {
+  using R = Rn<T>;
+  return R::add(R::add(R::add(d[a], d[b]), R::add(d[c], d[e])), d[f]);
+}
 
 template <typename T, bool FORCE, bool SCALED>
-__device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
+__device__ __forceinline__ void collide_f32(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
   using R = Rn<T>;
   T sum[10], dif[10];
 #pragma unroll
@@ -385,6 +411,133 @@ __device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv
       d[i + 1] = R::fma(K.al, dj, R::fma(K.be, di, Pm));
     }
   }
+}
+
+// FM: 0 no force, 1 force along x only (the zero terms of the other axes
+// dropped at compile time), 2 any force.
+template <typename T, int FM, bool SCALED>
+__device__ __forceinline__ void collide_f64_body(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
+  using R = Rn<T>;
+  // Moments from direction groups: P_a / M_a sum the d_i with c_ia = +1 / -1,
+  // j_a = P_a - M_a, rho - 1 = P_x + M_x + (the nine d_i with c_ix = 0).
+  // 37 additions for the four moments.
+  const T px = sum5(d, 1, 7, 9, 11, 13), mx = sum5(d, 2, 8, 10, 12, 14);
+  const T py = sum5(d, 3, 7, 10, 15, 17), my = sum5(d, 4, 8, 9, 16, 18);
+  const T pz = sum5(d, 5, 11, 14, 15, 18), mz = sum5(d, 6, 12, 13, 16, 17);
+  const T x0 = R::add(R::add(R::add(R::add(d[3], d[4]), R::add(d[5], d[6])),
+                             R::add(R::add(d[15], d[16]), R::add(d[17], d[18]))),
+                      d[0]);
+  const T sdrho = R::add(R::add(px, mx), x0);
+  const T sjx = R::sub(px, mx), sjy = R::sub(py, my), sjz = R::sub(pz, mz);
+  const T drho = SCALED ? R::mul(sdrho, inv_s) : sdrho;
+  const T rho = R::add(T(1), drho);
+  const T srho = SCALED ? R::mul(s, rho) : rho;
+  // J = j + rho g / 2 = rho u, kept in the stored units (s J)
+  constexpr bool FORCE = FM != 0;
+  T sJx = sjx, sJy = sjy, sJz = sjz;
+  if (FORCE) sJx = R::fma(srho, K.hg[0], sjx);
+  if (FM == 2) {
+    sJy = R::fma(srho, K.hg[1], sjy);
+    sJz = R::fma(srho, K.hg[2], sjz);
+  }
+  const T inv = SCALED ? R::mul(recip(rho), inv_s) : recip(rho);  // 1 / (s rho)
+  drho_out = drho;
+  rjx_out = SCALED ? R::mul(sJx, inv_s) : sJx;
+  // The velocity itself is never formed: with u = sJ / (s rho),
+  //   s rho u.u = |sJ|^2 inv,  s rho u.g = sJ.g,  s rho (c.u) = c.sJ,
+  //   c.u = (c.sJ) inv,
+  // so each opposite pair needs c.sJ alone (additions of the momentum sums).
+  const T J2 = R::fma(sJz, sJz, R::fma(sJy, sJy, R::mul(sJx, sJx)));
+  T sA = R::fma(-R::mul(K.q15, inv), J2, R::mul(K.lp, sdrho));  // s * A
+  if (FORCE) {
+    const T Jg = FM == 1 ? R::mul(sJx, K.g[0]) : R::fma(sJz, K.g[2], R::fma(sJy, K.g[1], R::mul(sJx, K.g[0])));
+    sA = R::fma(-K.q3, Jg, sA);
+  }
+  d[0] = R::fma(K.om1, d[0], R::mul(T(WD(0)), sA));
+  const T wsA[2] = {R::mul(T(WD(1)), sA), R::mul(T(WD(7)), sA)};
+  const T tpi[2] = {R::mul(K.tp[0], inv), R::mul(K.tp[1], inv)};  // tp_c / (s rho)
+  // c_i . v in the fixed order x, y, z
+  auto dot = [&](int i, T vx, T vy, T vz) {
+    T r = 0;
+    bool first = true;
+    if (CX(i)) { r = CX(i) > 0 ? vx : -vx; first = false; }
+    if (CY(i)) { r = first ? (CY(i) > 0 ? vy : -vy) : (CY(i) > 0 ? R::add(r, vy) : R::sub(r, vy)); first = false; }
+    if (CZ(i)) { r = first ? (CZ(i) > 0 ? vz : -vz) : (CZ(i) > 0 ? R::add(r, vz) : R::sub(r, vz)); }
+    return r;
+  };
+  // For pair k with P = s (w A + rho (c.u)(tp_c c.u + fp_k)) and
+  // M = s rho (tm_c c.u + fm_k), the two sums are formed directly from
+  // sc = c.sJ = s rho c.u:
+  //   P +- M = wsA +- s rho fm_k + sc (tp_c inv sc + (fp_k +- tm_c))
+  // (without a force: wsA + sc (tp_c inv sc +- tm_c)).
+  auto terms = [&](int k, T &Pp, T &Pm) {
+    const int i = 2 * k - 1;
+    const int c = i <= 6 ? 0 : 1;
+    const T sc = dot(i, sJx, sJy, sJz);
+    if (FORCE) {
+      // fm_k = 0 when c.g = 0: with g along x, for the pairs with c_x = 0
+      T bp = wsA[c], bm = wsA[c];
+      if (FM == 2 || CX(i) != 0) {
+        bp = R::fma(srho, K.fm[k], wsA[c]);
+        bm = R::fma(-srho, K.fm[k], wsA[c]);
+      }
+      Pp = R::fma(sc, R::fma(tpi[c], sc, K.zp[k]), bp);
+      Pm = R::fma(sc, R::fma(tpi[c], sc, K.zm[k]), bm);
+    } else {
+      Pp = R::fma(sc, R::fma(tpi[c], sc, K.tm[c]), wsA[c]);
+      Pm = R::fma(sc, R::fma(tpi[c], sc, -K.tm[c]), wsA[c]);
+    }
+  };
+  if (K.bgk) {
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      const int i = 2 * k - 1;
+      T Pp, Pm;
+      terms(k, Pp, Pm);
+      d[i] = R::fma(K.om1, d[i], Pp);
+      d[i + 1] = R::fma(K.om1, d[i + 1], Pm);
+    }
+  } else {
+    // a* +- b* with a = (d_i + d_opp)/2, b = (d_i - d_opp)/2 expanded, so
+    // that only d_i and d_opp stay live:
+    //   d*_i = al d_i + be d_opp + (P + M),  d*_opp = be d_i + al d_opp + (P - M)
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      const int i = 2 * k - 1;
+      T Pp, Pm;
+      terms(k, Pp, Pm);
+      const T di = d[i], dj = d[i + 1];
+      d[i] = R::fma(K.al, di, R::fma(K.be, dj, Pp));
+      d[i + 1] = R::fma(K.al, dj, R::fma(K.be, di, Pm));
+    }
+  }
+}
+
+template <typename T, bool FORCE, bool SCALED>
+__device__ __forceinline__ void collide_f64(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
+  // one uniform branch per node (a kernel parameter or a segment's
+  // constants), so the force terms that are zero cost no FP64 instruction
+  if (!FORCE)
+    collide_f64_body<T, 0, SCALED>(d, K, s, inv_s, drho_out, rjx_out);
+  else if (K.gx_only)
+    collide_f64_body<T, 1, SCALED>(d, K, s, inv_s, drho_out, rjx_out);
+  else
+    collide_f64_body<T, 2, SCALED>(d, K, s, inv_s, drho_out, rjx_out);
+}
+
+// Two evaluations of the same collision.  FP64 runs on GB300's narrow FP64
+// pipe (two thread instructions per SM clock), which bounds every FP64 step
+// kernel: collide_f64 minimises FP64 instructions (velocity never formed,
+// direction-group moments, a Newton reciprocal; ncu: 114 per update without
+// a force).  FP32 arithmetic is cheap, the FP32 and FP16 kernels are bound by
+// memory and issue rate within 64-85 registers: collide_f32 keeps fewer
+// values live (u instead of J and 1/rho).
+template <typename T, bool FORCE, bool SCALED>
+__device__ __forceinline__ void collide(T (&d)[Q], const CollK<T> &K, T s, T inv_s, T &drho_out, T &rjx_out) {
+  if constexpr (sizeof(T) == 8)
+    collide_f64<T, FORCE, SCALED>(d, K, s, inv_s, drho_out, rjx_out);
+  else
+    collide_f32<T, FORCE, SCALED>(d, K, s, inv_s, drho_out, rjx_out);
 }
 
 // The collision in the units a codec's step kernels load: S * d_i for F16S,
@@ -570,9 +723,11 @@ struct IndirectNode {
 };
 
 // ---------------------------------------------------------------------------
-// Block reduction of (mass, flux) into per-block FP64 partials.
-// Works for 1D, 2D and 3D blocks and grids (block id in launch order).
-__device__ __forceinline__ void block_reduce_store(double m, double j, double *partials) {
+// Block reduction of (mass, flux) into FP64 partials[2 index], [2 index + 1]
+// (a fixed order: warp trees, then the warps in order).  Ends with a block
+// barrier, so a block may call it again (one partial per work chunk).
+// Works for 1D, 2D and 3D blocks.
+__device__ __forceinline__ void block_reduce_store_at(double m, double j, double *partials, int64_t index) {
   __shared__ double sm[32], sj[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -596,11 +751,17 @@ __device__ __forceinline__ void block_reduce_store(double m, double j, double *p
       j += __shfl_xor_sync(0xffffffffu, j, o);
     }
     if (lane == 0) {
-      const int64_t b = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-      partials[2 * b] = m;
-      partials[2 * b + 1] = j;
+      partials[2 * index] = m;
+      partials[2 * index + 1] = j;
     }
   }
+  __syncthreads();
+}
+
+// The same with the block's id in launch order as the index.
+__device__ __forceinline__ void block_reduce_store(double m, double j, double *partials) {
+  block_reduce_store_at(m, j, partials,
+                        blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z));
 }
 
 }  // namespace lbmk

@@ -28,8 +28,11 @@ constexpr int kMaxBlocks = LBM_NOALLOC_MAX_BLOCKS;
 // Partial (mass, flux) of each block; see the header comment.
 static __device__ __align__(256) double g_noalloc_partials[2 * kMaxBlocks];
 
-// Device address of g_noalloc_partials, per device, found once with that
-// device current (host code may not use the symbol itself as an address).
+// Device address of g_noalloc_partials, per device (host code may not use the
+// symbol itself as an address).  Looked up again on every call made outside
+// a stream capture, so a new context on the device (after cudaDeviceReset,
+// which reloads the module) never meets a stale address; a call under
+// capture uses the address of the last call on the device.
 std::mutex g_mutex;
 constexpr int kMaxDevices = 64;
 double *g_scratch[kMaxDevices] = {nullptr};
@@ -42,7 +45,7 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_partials(const typename C:
   // block b sums nodes [b * chunk, (b + 1) * chunk): a fixed assignment, so
   // the result depends only on n and the chunk size
   const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;  // the last block's chunk may be partial
   double m = 0.0, j = 0.0;
   for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
     double rho = 0.0, jx = 0.0;
@@ -87,21 +90,38 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_final(const double *partia
   }
 }
 
-// One-time set-up on the current device: the device address of the scratch.
-cudaError_t scratch_for_current_device(double **ptr) {
+// The device address of the scratch on the current device: queried with the
+// device current when the stream is not capturing (and cached), taken from
+// the cache under capture (cudaErrorStreamCaptureUnsupported when no call
+// outside a capture came first on this device).
+cudaError_t scratch_for_current_device(cudaStream_t s, double **ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_scratch[dev] = static_cast<double *>(p);
+  } else if (!g_scratch[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *ptr = g_scratch[dev];
   return cudaSuccess;
+}
+
+// Nodes per block: at least LBM_NOALLOC_MIN_CHUNK, at most
+// LBM_NOALLOC_MAX_BLOCKS blocks, a multiple of the block size.  A function
+// of n alone, so the summation order (and the result's bits) is too.
+int64_t chunk_of(int64_t n) {
+  int64_t c = (n + kMaxBlocks - 1) / kMaxBlocks;
+  c = (c + kThreads - 1) / kThreads * kThreads;
+  return c > LBM_NOALLOC_MIN_CHUNK ? c : LBM_NOALLOC_MIN_CHUNK;
 }
 
 template <class C>
@@ -125,17 +145,18 @@ extern "C" lbm_status lbm_flux_noalloc(const void *f_dev, int32_t precision, int
     return LBM_ERR_INVALID_ARG;
   if (layout == LBM_SOA && npad < n) return LBM_ERR_INVALID_ARG;
   if (precision == LBM_F16S && !(f16_scale > 0.0)) return LBM_ERR_INVALID_ARG;
-  if (n > (int64_t)kMaxBlocks * LBM_NOALLOC_CHUNK) return LBM_ERR_INVALID_ARG;  // beyond the scratch
-  double *scratch = nullptr;
-  if (scratch_for_current_device(&scratch) != cudaSuccess) return LBM_ERR_CUDA;
-  const int nblocks = (int)((n + LBM_NOALLOC_CHUNK - 1) / LBM_NOALLOC_CHUNK);
-  const float inv = precision == LBM_F16S ? (float)(1.0 / f16_scale) : 1.0f;
+  if (n > LBM_NOALLOC_MAX_NODES) return LBM_ERR_INVALID_ARG;  // beyond the scratch
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *scratch = nullptr;
+  if (scratch_for_current_device(s, &scratch) != cudaSuccess) return LBM_ERR_CUDA;
+  const int64_t chunk = chunk_of(n);
+  const int nblocks = (int)((n + chunk - 1) / chunk);
+  const float inv = precision == LBM_F16S ? (float)(1.0 / f16_scale) : 1.0f;
   if (precision == LBM_F64)
-    launch<lbmk::CodecF64>(layout, f_dev, n, npad, LBM_NOALLOC_CHUNK, nblocks, inv, gx, scratch, out_dev, s);
+    launch<lbmk::CodecF64>(layout, f_dev, n, npad, chunk, nblocks, inv, gx, scratch, out_dev, s);
   else if (precision == LBM_F32)
-    launch<lbmk::CodecF32>(layout, f_dev, n, npad, LBM_NOALLOC_CHUNK, nblocks, inv, gx, scratch, out_dev, s);
+    launch<lbmk::CodecF32>(layout, f_dev, n, npad, chunk, nblocks, inv, gx, scratch, out_dev, s);
   else
-    launch<lbmk::CodecF16S>(layout, f_dev, n, npad, LBM_NOALLOC_CHUNK, nblocks, inv, gx, scratch, out_dev, s);
+    launch<lbmk::CodecF16S>(layout, f_dev, n, npad, chunk, nblocks, inv, gx, scratch, out_dev, s);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -9,7 +9,6 @@
 
 #include "lbm_dispatch.cuh"
 #include "lbm_internal.h"
-#include "lbm_pair.cuh"
 
 namespace lbmk {
 
@@ -801,8 +800,8 @@ struct LaunchOS {
     go<false>(p, sub & 1, L);
   }
 };
-// sub: 0 even, 1 odd (one node per thread); 2 even, 3 odd (x pairs, SoA full
-// grid); 4 even, 5 odd (z pairs, FP16 / FP32 storage, SoA full grid)
+// sub: 0 even, 1 odd (one node per thread); 4 even, 5 odd (z pairs, FP16 /
+// FP32 storage, SoA full grid)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
@@ -812,15 +811,6 @@ struct LaunchAA {
           k_aa_odd_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
         else
           k_aa_even_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
-      }
-      return;
-    }
-    if (sub >= 2) {
-      if constexpr (AOS == 0 && !IND) {
-        if (sub == 3)
-          k_aa2_odd<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
-        else
-          k_aa2_even<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
       }
       return;
     }

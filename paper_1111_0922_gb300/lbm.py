@@ -44,7 +44,7 @@ class lbm_config(ctypes.Structure):
                 ("omega", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("f16_scale", ctypes.c_double), ("trt_magic", ctypes.c_double),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
-                ("cg_shift", ctypes.c_int32), ("pair_x", ctypes.c_int32),
+                ("cg_shift", ctypes.c_int32),
                 ("store_hint", ctypes.c_int32), ("swap_schedule", ctypes.c_int32),
                 ("pair_z", ctypes.c_int32),
                 ("stream", ctypes.c_void_p),
@@ -65,6 +65,7 @@ class lbm_batch_config(ctypes.Structure):
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
                 ("capacity_slots", ctypes.c_int64), ("max_geometries", ctypes.c_int32),
                 ("keep_idx", ctypes.c_int32), ("f16_scale", ctypes.c_double),
+                ("tune_variant", ctypes.c_int32), ("round_mode", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -74,7 +75,7 @@ class lbm_batch_info(ctypes.Structure):
                 ("largest_free", ctypes.c_int64), ("active_nodes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("active_geometries", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("nodes_per_thread", ctypes.c_int32),
-                ("work_chunks", ctypes.c_int32)]
+                ("work_chunks", ctypes.c_int32), ("variant", ctypes.c_int32), ("round_mode", ctypes.c_int32)]
 
 
 # exported symbols and their signatures (every function declared in lbm.h)
@@ -101,21 +102,29 @@ SIGNATURES = {
     "lbm_flux": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "lbm_macroscopics": (_I, [_P, _P, _P, _I]),
     "lbm_sync": (_I, [_P]),
+    "lbm_solve_permeability": (_I, [_P, ctypes.c_int32, ctypes.c_double, _I64, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int64)]),
     "lbm_batch_bytes_per_slot": (_I64, [ctypes.c_int32, ctypes.c_int32]),
     "lbm_batch_create": (_I, [ctypes.POINTER(lbm_batch_config), ctypes.POINTER(_P)]),
     "lbm_batch_destroy": (_I, [_P]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
-    "lbm_batch_admit_spheres": (_I, [_P, _P, _P, _I64, _P, _I64, _I64, ctypes.c_double, _P,
+    "lbm_batch_admit": (_I, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_double, _P,
+                             ctypes.c_double, _I64, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_admit_spheres": (_I, [_P, _P, _P, _I64, _P, _I64, _I64, ctypes.c_double, _P, ctypes.c_double, _I64,
                                      ctypes.POINTER(ctypes.c_int32)]),
     "lbm_batch_release": (_I, [_P, ctypes.c_int32]),
     "lbm_batch_round": (_I, [_P, ctypes.c_int32]),
-    "lbm_batch_poll": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+    "lbm_batch_poll": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_batch_flux": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "lbm_batch_slot_info": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "lbm_batch_get_info": (_I, [_P, ctypes.POINTER(lbm_batch_info)]),
     "lbm_batch_get_pdfs": (_I, [_P, ctypes.c_int32, _P]),
     "lbm_batch_tune": (_I, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "lbm_flux_noalloc": (_I, [_P, ctypes.c_int32, ctypes.c_int32, _I64, _I64, ctypes.c_double,
                               ctypes.c_double, _P, _P]),
@@ -276,6 +285,17 @@ def lbm_sync(h):
     _check(h, load().lbm_sync(h))
 
 
+def lbm_solve_permeability(h, check=100, tol=1e-6, max_steps=200000):
+    """Run to a steady flux in the library (see include/lbm.h); returns
+    (permeability, mass, flux, steps, converged)."""
+    k, m, f, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    st = load().lbm_solve_permeability(h, int(check), float(tol), int(max_steps), ctypes.byref(k), ctypes.byref(m),
+                                       ctypes.byref(f), ctypes.byref(n))
+    if st not in (LBM_OK, LBM_ERR_NOT_CONVERGED):
+        _check(h, st)
+    return k.value, m.value, f.value, n.value, st == LBM_OK
+
+
 def lbm_flux_noalloc(f_dev, precision, layout, n, npad, f16_scale, gx, out_dev, stream=None):
     """Mass and flux of a caller-owned natural PDF array into out_dev (2
     doubles on the device), for callers that cannot allocate device memory:
@@ -327,7 +347,7 @@ class Lattice:
 
     def __init__(self, dims, periodic=(1, 1, 1), variant="aa", addressing="direct",
                  layout="soa", precision="f32", omega=1.0, force=(0.0, 0.0, 0.0),
-                 f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0, pair_x=0,
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, cg_shift=0,
                  trt_magic=0.0, store_hint=0, swap_schedule=0, pair_z=0, stream=None, use_torch_allocator=True):
         self.cfg = lbm_config_default()
         c = self.cfg
@@ -346,7 +366,6 @@ class Lattice:
         c.block_size = int(block_size)
         c.nodes_per_thread = int(nodes_per_thread)
         c.cg_shift = int(cg_shift)
-        c.pair_x = int(pair_x)
         c.store_hint = int(store_hint)
         c.swap_schedule = int(swap_schedule)
         c.pair_z = int(pair_z)
@@ -427,6 +446,9 @@ class Lattice:
     def sync(self):
         lbm_sync(self.h)
 
+    def solve_permeability(self, check=100, tol=1e-6, max_steps=200000):
+        return lbm_solve_permeability(self.h, check, tol, max_steps)
+
 
 # ---------------------------------------------------------------------------
 # Batches (continuous batching of many geometries)
@@ -451,14 +473,26 @@ def lbm_batch_destroy(b):
     _bcheck(None, load().lbm_batch_destroy(b))
 
 
-def lbm_batch_admit_spheres(b, dims, periodic, centres, radius, unit, omega, force):
+def lbm_batch_admit(b, mask, dims, periodic, omega, force, tol=1e-6, max_steps=0):
+    m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+    if m.size != int(np.prod(dims)):
+        raise ValueError("mask has %d cells, box %s" % (m.size, tuple(dims)))
+    p = (ctypes.c_int32 * 3)(*[int(v) for v in periodic])
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    slot = ctypes.c_int32()
+    _bcheck(b, load().lbm_batch_admit(b, _ptr(m), int(dims[0]), int(dims[1]), int(dims[2]), p, float(omega), f,
+                                      float(tol), int(max_steps), ctypes.byref(slot)))
+    return slot.value
+
+
+def lbm_batch_admit_spheres(b, dims, periodic, centres, radius, unit, omega, force, tol=1e-6, max_steps=0):
     d = (ctypes.c_int32 * 3)(*[int(v) for v in dims])
     p = (ctypes.c_int32 * 3)(*[int(v) for v in periodic])
     f = (ctypes.c_double * 3)(*[float(v) for v in force])
     c = np.ascontiguousarray(np.asarray(centres, dtype=np.int64).reshape(-1, 3))
     slot = ctypes.c_int32()
     _bcheck(b, load().lbm_batch_admit_spheres(b, d, p, c.shape[0], _ptr(c), int(radius), int(unit),
-                                              float(omega), f, ctypes.byref(slot)))
+                                              float(omega), f, float(tol), int(max_steps), ctypes.byref(slot)))
     return slot.value
 
 
@@ -471,8 +505,16 @@ def lbm_batch_round(b, k):
 
 
 def lbm_batch_poll(b, slot):
+    """(done, permeability, steps): done 0 running, 1 steady, 2 step cap."""
+    d, k, n = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int64()
+    _bcheck(b, load().lbm_batch_poll(b, int(slot), ctypes.byref(d), ctypes.byref(k), ctypes.byref(n)))
+    return d.value, k.value, n.value
+
+
+def lbm_batch_flux(b, slot):
+    """(mass, flux, steps) of the state the last round started from."""
     m, f, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-    _bcheck(b, load().lbm_batch_poll(b, int(slot), ctypes.byref(m), ctypes.byref(f), ctypes.byref(s)))
+    _bcheck(b, load().lbm_batch_flux(b, int(slot), ctypes.byref(m), ctypes.byref(f), ctypes.byref(s)))
     return m.value, f.value, s.value
 
 
@@ -495,18 +537,20 @@ def lbm_batch_get_pdfs(b, slot, nodes):
 
 
 def lbm_batch_tune(b, rounds=2, k=10):
-    bs, npt, mf = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _bcheck(b, load().lbm_batch_tune(b, int(rounds), int(k), ctypes.byref(bs), ctypes.byref(npt),
-                                     ctypes.byref(mf)))
-    return bs.value, npt.value, mf.value
+    """(variant, block size, nodes per thread, round mode, MFLUP/s) of the
+    fastest candidate; every geometry restarts from rest."""
+    v, bs, npt, mode, mf = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _bcheck(b, load().lbm_batch_tune(b, int(rounds), int(k), ctypes.byref(v), ctypes.byref(bs), ctypes.byref(npt),
+                                     ctypes.byref(mode), ctypes.byref(mf)))
+    return v.value, bs.value, npt.value, mode.value, mf.value
 
 
 class Batch:
     """Many sphere-pack geometries on one GPU, advanced together in rounds."""
 
     def __init__(self, capacity_slots, variant="aa", precision="f32", max_geometries=1024,
-                 f16_scale=0.0, block_size=0, nodes_per_thread=0, keep_idx=0, stream=None,
-                 use_torch_allocator=True):
+                 f16_scale=0.0, block_size=0, nodes_per_thread=0, keep_idx=0, tune_variant=0, round_mode=0,
+                 stream=None, use_torch_allocator=True):
         cfg = lbm_batch_config()
         cfg.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -516,6 +560,8 @@ class Batch:
         cfg.max_geometries = int(max_geometries)
         cfg.f16_scale = float(f16_scale)
         cfg.keep_idx = int(keep_idx)
+        cfg.tune_variant = int(tune_variant)
+        cfg.round_mode = int(round_mode)
         self._alloc = None
         if stream is None or use_torch_allocator:
             import torch
@@ -542,9 +588,14 @@ class Batch:
         except Exception:  # noqa: BLE001
             pass
 
-    def admit(self, pack, omega, force):
+    def admit(self, pack, omega, force, tol=1e-6, max_steps=0):
+        """Admit a sphere pack (inputs.SpherePack)."""
         return lbm_batch_admit_spheres(self.b, pack.dims, pack.periodic, pack.centres, pack.radius,
-                                       pack.unit, omega, force)
+                                       pack.unit, omega, force, tol, max_steps)
+
+    def admit_mask(self, mask, dims, periodic, omega, force, tol=1e-6, max_steps=0):
+        """Admit a geometry given as a solid mask (x fastest, nonzero = solid)."""
+        return lbm_batch_admit(self.b, mask, dims, periodic, omega, force, tol, max_steps)
 
     def release(self, slot):
         lbm_batch_release(self.b, slot)
@@ -553,7 +604,12 @@ class Batch:
         lbm_batch_round(self.b, k)
 
     def poll(self, slot):
+        """(done, permeability, steps) after the last round."""
         return lbm_batch_poll(self.b, slot)
+
+    def flux(self, slot):
+        """(mass, flux, steps) of the state the last round started from."""
+        return lbm_batch_flux(self.b, slot)
 
     def slot_info(self, slot):
         return lbm_batch_slot_info(self.b, slot)
@@ -566,4 +622,5 @@ class Batch:
         return lbm_batch_get_pdfs(self.b, slot, self.slot_info(slot)[0])
 
     def tune(self, rounds=2, k=10):
+        """(variant, block size, nodes per thread, round mode, MFLUP/s)."""
         return lbm_batch_tune(self.b, rounds, k)

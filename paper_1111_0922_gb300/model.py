@@ -83,39 +83,63 @@ def roof_mflups(variant: str, indirect: bool, precision: str, hbm_gbs: float) ->
     return hbm_gbs * 1e9 / gpu_bytes(variant, indirect, precision) / 1e6
 
 
-# FP64 instruction roof on GB300: 2 FP64 thread-instructions per clock per SM
-# (ncu's sm__sass_thread_inst_executed_op_dfma_pred_on peak) on 152 SMs at the
-# 2.07 GHz maximum SM clock.  The BGK collision issues 127 FP64 instructions
-# per update without a body force (ncu, AA pattern on 256^3: 46 DADD, 63
-# DFMA, 18 DMUL per node); counted from the source, a force adds 16 (u, u.g,
-# one more operation per opposite pair) and TRT adds 18 (two more operations
-# per opposite pair).
-FP64_INST_PER_CLK_SM = 2
-GB300_SMS = 152
-GB300_SM_GHZ = 2.07
-FP64_INST_BGK = 127
+# FP64-pipe roof.  GB300 runs FP64 arithmetic on a narrow pipe (two thread
+# instructions per SM clock), so every FP64 step kernel is bound by its FP64
+# instruction count per update, not by HBM.  Every input of this roof is
+# measured, none is a constant of this module: the SM count is the device's
+# attribute, the SM clock the median sampled during the timed region, and
+# the pipe's peak rate and the instructions per update (DADD + DMUL + DFMA
+# thread instructions of the collision, one count per collision kind) come
+# from an ncu capture whose summary is committed under profiles/.
+COLLISIONS = ("bgk", "bgk_force", "trt_force")
 
 
-def fp64_inst_per_flup(force: bool = False, trt: bool = False) -> int:
-    return FP64_INST_BGK + (16 if force else 0) + (18 if trt else 0)
+def collision_kind(force: bool = False, trt: bool = False) -> str:
+    if trt and not force:
+        raise ValueError("no captured FP64 count for TRT without a body force")
+    return "trt_force" if trt else ("bgk_force" if force else "bgk")
 
 
-def fp64_roof_mflups(force: bool = False, trt: bool = False) -> float:
-    """FP64-pipe roofline in MFLUP/s of an FP64 step (any scheme)."""
-    rate = FP64_INST_PER_CLK_SM * GB300_SMS * GB300_SM_GHZ * 1e9
-    return rate / fp64_inst_per_flup(force, trt) / 1e6
+class Fp64Pipe:
+    """FP64-pipe roof from measured inputs.
+
+    sms              streaming multiprocessors (device attribute)
+    sm_ghz           SM clock during the timed region (GHz)
+    inst_per_clk_sm  peak FP64 thread instructions per SM clock (ncu's
+                     sm__thread_inst_executed_pipe_fp64_pred_on peak)
+    inst_per_flup    {collision kind: FP64 thread instructions per update}
+                     (ncu: the kernel's DADD + DMUL + DFMA thread instructions
+                     divided by the nodes of the launch)
+    """
+
+    def __init__(self, sms: int, sm_ghz: float, inst_per_clk_sm: float, inst_per_flup: dict):
+        self.sms = int(sms)
+        self.sm_ghz = float(sm_ghz)
+        self.inst_per_clk_sm = float(inst_per_clk_sm)
+        self.inst_per_flup = dict(inst_per_flup)
+
+    def inst_rate(self) -> float:
+        """Peak FP64 thread instructions per second of the whole GPU."""
+        return self.sms * self.inst_per_clk_sm * self.sm_ghz * 1e9
+
+    def roof_mflups(self, force: bool = False, trt: bool = False) -> float:
+        return self.inst_rate() / self.inst_per_flup[collision_kind(force, trt)] / 1e6
+
+    def as_dict(self) -> dict:
+        return {"sms": self.sms, "sm_ghz": self.sm_ghz, "inst_per_clk_sm": self.inst_per_clk_sm,
+                "inst_per_flup": self.inst_per_flup}
 
 
-def bound_roof(variant: str, indirect: bool, precision: str, hbm_gbs: float, force: bool = False,
-               trt: bool = False):
+def bound_roof(variant: str, indirect: bool, precision: str, hbm_gbs: float, fp64: Fp64Pipe | None = None,
+               force: bool = False, trt: bool = False):
     """(bound, roof MFLUP/s): the lower of the HBM and, for FP64, FP64-pipe
-    roofs.  The two-step scheme's FP64 roof adds the time of its stream
-    kernel (pure data movement, half of its bytes at HBM speed) to the
-    collide kernel's FP64-pipe time, since the two kernels run one after the
-    other."""
+    roofs (the latter only when `fp64` is given).  The two-step scheme's
+    FP64 roof adds the time of its stream kernel (pure data movement, half
+    of its bytes at HBM speed) to the collide kernel's FP64-pipe time, since
+    the two kernels run one after the other."""
     hbm = roof_mflups(variant, indirect, precision, hbm_gbs)
-    if precision == "f64":
-        alu = fp64_roof_mflups(force, trt)
+    if precision == "f64" and fp64 is not None:
+        alu = fp64.roof_mflups(force, trt)
         if variant == "ts":
             stream_s = gpu_bytes(variant, indirect, precision) / 2 / (hbm_gbs * 1e9)
             alu = 1.0 / (1.0 / (alu * 1e6) + stream_s) / 1e6

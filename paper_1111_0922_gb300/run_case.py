@@ -41,7 +41,7 @@ def setup(args):
     dims = (size, size, size)
     common = dict(variant=args.variant, addressing=args.addressing, layout=args.layout,
                   precision=args.precision, block_size=args.block_size,
-                  nodes_per_thread=args.nodes_per_thread, pair_x=args.pair_x,
+                  nodes_per_thread=args.nodes_per_thread,
                   store_hint=args.store_hint, swap_schedule=args.swap_schedule, pair_z=args.pair_z,
                   trt_magic=3.0 / 16.0 if args.trt else 0.0)
     if kind == "dense":
@@ -88,7 +88,6 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--nodes-per-thread", type=int, default=0)
-    ap.add_argument("--pair-x", type=int, default=0, help="AA on a full grid: 1 = two x-adjacent nodes per thread")
     ap.add_argument("--store-hint", type=int, default=0,
                     help="OS push/pull, SoA: 1 = cache-streaming stores of the second lattice (OS-NT analogue)")
     ap.add_argument("--swap-schedule", type=int, default=0,

@@ -3,10 +3,13 @@
 Requests (a sphere-pack geometry, omega, force) arrive over time.  They are
 admitted into a shared batch of node-list segments as device memory frees up
 (the batch's capacity is the HBM budget divided by the bytes per node slot),
-advanced together in rounds of `k_round` steps, and retired when their flux
-has converged (relative change below `tol` between two rounds).  Each round's
-first step also reduces every geometry's flux, so convergence checks cost no
-extra pass.  Reports latency (arrival to result) and throughput.
+advanced together in rounds of `k_round` steps, and retired when the library
+reports their flux steady (relative change below `tol` between two rounds) or
+their step cap reached; the permeability comes from the library too.  Each
+round's first step also reduces every geometry's flux, so convergence checks
+cost no extra pass.  Admission runs while a round is in flight: the geometry
+is built on the library's second stream and joins the next round.  Reports
+latency (arrival to result) and throughput.
 
 The engine is anything with the small interface of `BatchEngine` (the GPU
 batch); tests drive the same loop with a CPU stand-in and a simulated clock.
@@ -19,7 +22,6 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import inputs
-from .permeability import permeability
 
 
 @dataclass
@@ -53,7 +55,6 @@ class _Active:
     slot: int
     admitted: float
     nodes: int
-    prev: float | None = None
 
 
 class RealClock:
@@ -93,17 +94,17 @@ class BatchEngine:
     """The GPU batch (lbm.Batch) behind the serving interface."""
 
     def __init__(self, capacity_slots, variant="aa", precision="f16s", f16_scale=2.0 ** 22,
-                 max_geometries=4096, block_size=0, nodes_per_thread=0):
+                 max_geometries=4096, block_size=0, nodes_per_thread=0, round_mode=0):
         from . import lbm
 
         self.lbm = lbm
         self.batch = lbm.Batch(capacity_slots, variant=variant, precision=precision,
                                max_geometries=max_geometries, f16_scale=f16_scale,
-                               block_size=block_size, nodes_per_thread=nodes_per_thread)
+                               block_size=block_size, nodes_per_thread=nodes_per_thread, round_mode=round_mode)
 
-    def admit(self, req: Request) -> tuple[int, int]:
+    def admit(self, req: Request, tol: float, max_steps: int) -> tuple[int, int]:
         try:
-            slot = self.batch.admit(req.pack, req.omega, req.force)
+            slot = self.batch.admit(req.pack, req.omega, req.force, tol, max_steps)
         except self.lbm.LBMError as e:
             if e.status == self.lbm.LBM_ERR_OOM:
                 raise OutOfCapacity(str(e)) from e
@@ -115,10 +116,12 @@ class BatchEngine:
         self.batch.release(slot)
 
     def round(self, k: int) -> None:
+        """Enqueue k steps of every active geometry (returns at once)."""
         self.batch.round(k)
 
     def poll(self, slot: int):
-        """(mass, flux, steps) of the last round for this slot."""
+        """(done, permeability, steps) after the last round: done 0 running,
+        1 steady, 2 step cap."""
         return self.batch.poll(slot)
 
     def close(self):
@@ -154,10 +157,12 @@ def serve(requests, engine, clock=None, k_round: int = 100, tol: float = 1e-6, m
           on_round=None) -> ServeStats:
     """Run the requests (sorted by arrival) to completion through `engine`.
 
-    Each loop iteration: admit every arrived request that fits (FIFO; a
-    request that does not fit waits and blocks the ones behind it), run one
-    round on every active geometry, then retire the converged ones and those
-    at `max_steps` (reported with converged = False)."""
+    Each loop iteration: enqueue one round on every active geometry; while it
+    runs, admit every arrived request that fits (FIFO; a request that does
+    not fit waits and blocks the ones behind it), so its geometry build
+    overlaps the round; then read the round's results and retire the
+    geometries the engine reports steady or at `max_steps` (the latter with
+    converged = False).  The admitted requests join the next round."""
     clock = clock or RealClock()
     queue = sorted(requests, key=lambda r: r.arrival)
     qi = 0
@@ -165,12 +170,20 @@ def serve(requests, engine, clock=None, k_round: int = 100, tol: float = 1e-6, m
     stats = ServeStats()
     t_start = clock.now()
     while qi < len(queue) or active:
+        launched = bool(active)
+        if launched:
+            engine.round(k_round)
+            stats.rounds += 1
+            stats.node_updates += k_round * sum(a.nodes for a in active.values())
+            if on_round:
+                on_round(clock, k_round, active)
+        newly: dict[int, _Active] = {}
         now = clock.now()
         while qi < len(queue) and queue[qi].arrival <= now:
             try:
-                slot, nodes = engine.admit(queue[qi])
+                slot, nodes = engine.admit(queue[qi], tol, max_steps)
             except OutOfCapacity:
-                if not active:  # does not fit even in an empty engine: reject it
+                if not active and not newly:  # does not fit even in an empty engine: reject it
                     r = queue[qi]
                     stats.results.append(Result(r.rid, r.arrival, clock.now(), clock.now(), float("nan"), 0, 0,
                                                 False))
@@ -178,29 +191,20 @@ def serve(requests, engine, clock=None, k_round: int = 100, tol: float = 1e-6, m
                     qi += 1
                     continue
                 break
-            active[slot] = _Active(queue[qi], slot, clock.now(), nodes)
+            newly[slot] = _Active(queue[qi], slot, clock.now(), nodes)
             qi += 1
-        if not active:
-            if qi < len(queue):
-                clock.wait_until(queue[qi].arrival)
-            continue
-        engine.round(k_round)
-        stats.rounds += 1
-        stats.node_updates += k_round * sum(a.nodes for a in active.values())
-        if on_round:
-            on_round(clock, k_round, active)
-        for slot in list(active):
-            a = active[slot]
-            _, flux, steps = engine.poll(slot)
-            done = a.prev is not None and abs(flux - a.prev) < tol * abs(flux)
-            a.prev = flux
-            if done or steps >= max_steps:
-                cells = int(np.prod(a.req.pack.dims))
-                k = permeability(flux, cells, a.req.omega, a.req.force[0])
-                stats.results.append(Result(a.req.rid, a.req.arrival, a.admitted, clock.now(), k, int(steps),
-                                            a.nodes, bool(done)))
-                engine.release(slot)
-                del active[slot]
+        if launched:
+            for slot in list(active):
+                a = active[slot]
+                done, k, steps = engine.poll(slot)
+                if done:
+                    stats.results.append(Result(a.req.rid, a.req.arrival, a.admitted, clock.now(), k, int(steps),
+                                                a.nodes, done == 1))
+                    engine.release(slot)
+                    del active[slot]
+        active.update(newly)
+        if not active and qi < len(queue):
+            clock.wait_until(queue[qi].arrival)
     stats.wall = clock.now() - t_start
     return stats
 

@@ -39,13 +39,31 @@ def test_every_declared_symbol_is_exported(lib):
         assert name in lbm.SIGNATURES, "binding lacks %s" % name
 
 
-def test_struct_sizes(lib):
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct as the C compiler lays it out."""
+    import subprocess
+
+    src = tmp_path / "layout.c"
+    body = "".join('printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
+                   'int main(void) { printf("%%zu\\n", sizeof(%s)); %s return 0; }\n' % (struct, body))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["lbm_config", "lbm_info", "lbm_batch_config", "lbm_batch_info"])
+def test_struct_layouts_match_header(lib, tmp_path, name):
+    """Every ctypes struct of the binding has the size and field offsets the
+    C compiler gives the header's struct."""
     from paper_1111_0922_gb300 import lbm
 
-    # 3+3+4 int32, 6 doubles, 7 int32 (+4 bytes of padding), 4 pointers
-    assert ctypes.sizeof(lbm.lbm_config) == 10 * 4 + 6 * 8 + 7 * 4 + 4 + 4 * 8
-    # 6 int64, 2 int32, 1 double, 3 int32 (+4 bytes of padding)
-    assert ctypes.sizeof(lbm.lbm_info) == 6 * 8 + 2 * 4 + 8 + 3 * 4 + 4
+    cls = getattr(lbm, name)
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(tmp_path, name, fields)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
 
 
 def test_host_only_calls(lib):

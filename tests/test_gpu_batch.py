@@ -1,5 +1,8 @@
 """Batched geometries (continuous batching) against the oracle, and the
-same geometry alone and in a mix: bit-identical states and fluxes."""
+same geometry alone and in a mix, with one launch per step or one persistent
+launch per round: bit-identical states and fluxes.  Mask admission, the
+library's steady-flux test and permeability against the oracle's; the
+autotuner over variant, launch shape and round mode."""
 import numpy as np
 import pytest
 
@@ -34,17 +37,18 @@ def _oracle_steps(pack, omega, force, nsteps, f0=None):
     return oracle.run_sparse(idx, f, nsteps, omega, force), f
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("variant", ["aa", "et"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_batch_matches_oracle(L, variant, precision):
-    b = L.Batch(3 * 16384, variant=variant, precision=precision, max_geometries=8)
+def test_batch_matches_oracle(L, variant, precision, mode):
+    b = L.Batch(3 * 16384, variant=variant, precision=precision, max_geometries=8, round_mode=mode)
     slots = [b.admit(p, om, g) for p, om, g in _packs()]
     b.round(6)
     for s, (p, om, g) in zip(slots, _packs()):
         got = b.pdfs(s)
         ref, f0 = _oracle_steps(p, om, g, 6)
         m0, j0 = oracle.flux(f0, g)
-        m, j, steps = b.poll(s)
+        m, j, steps = b.flux(s)
         assert steps == 6
         # the fused sums add per-node moments from the collision, computed in
         # the storage's arithmetic (FP32: ~6e-8 relative each), in FP64
@@ -59,8 +63,12 @@ def test_batch_matches_oracle(L, variant, precision):
     b.close()
 
 
+@pytest.mark.parametrize("mix_mode", [0, 1])
 @pytest.mark.parametrize("variant", ["aa", "et"])
-def test_alone_equals_mix_bitwise(L, variant):
+def test_alone_equals_mix_bitwise(L, variant, mix_mode):
+    """One geometry alone (per-step launches, 256 x 1) and in a mix with
+    other geometries admitted earlier and later (another launch shape, either
+    round mode): the same bits."""
     packs = _packs()
     target = packs[0]
     alone = L.Batch(16384, variant=variant, precision="f32", max_geometries=4)
@@ -68,9 +76,9 @@ def test_alone_equals_mix_bitwise(L, variant):
     fl_alone = []
     for _ in range(3):
         alone.round(4)
-        fl_alone.append(alone.poll(s_alone))
-    mix = L.Batch(4 * 16384, variant=variant, precision="f32", max_geometries=8, block_size=128,
-                  nodes_per_thread=2)
+        fl_alone.append(alone.flux(s_alone))
+    mix = L.Batch(4 * 16384, variant=variant, precision="f32", max_geometries=8, block_size=512 if mix_mode else 128,
+                  nodes_per_thread=2, round_mode=mix_mode)
     other = mix.admit(*packs[1])
     mix.round(3)  # the other geometry is at an odd step count when the target arrives
     s_mix = mix.admit(*target)
@@ -78,8 +86,8 @@ def test_alone_equals_mix_bitwise(L, variant):
     fl_mix = []
     for _ in range(3):
         mix.round(4)
-        fl_mix.append(mix.poll(s_mix))
-    assert mix.poll(other)[2] == 15
+        fl_mix.append(mix.flux(s_mix))
+    assert mix.flux(other)[2] == 15
     assert fl_mix == fl_alone
     a = alone.pdfs(s_alone)
     m = mix.pdfs(s_mix)
@@ -115,15 +123,108 @@ def test_release_reuse_and_capacity(L):
     b.close()
 
 
-def test_tuner_picks_a_valid_shape(L):
+@pytest.mark.parametrize("tune_variant", [0, 1])
+def test_tuner_picks_a_valid_configuration(L, tune_variant):
+    """The autotuner returns one of its candidates, leaves every geometry at
+    rest in it, and the tuned batch then matches the oracle."""
     packs = _packs()
-    b = L.Batch(3 * 16384, variant="aa", precision="f32", max_geometries=4)
-    for p in packs:
-        b.admit(*p)
-    bs, npt, mflups = b.tune(rounds=1, k=4)
-    assert bs in (64, 128, 256) and npt in (1, 2, 4) and mflups > 0
-    assert (b.info.block_size, b.info.nodes_per_thread) == (bs, npt)
+    b = L.Batch(4 * 16384, variant="aa", precision="f32", max_geometries=4, tune_variant=tune_variant)
+    slots = [b.admit(*p) for p in packs]
+    b.round(3)
+    v, bs, npt, mode, mflups = b.tune(rounds=1, k=4)
+    assert v in ((L.LBM_AA, L.LBM_ET) if tune_variant else (L.LBM_AA,))
+    assert bs in (128, 256, 512) and npt in (1, 2, 4, 8) and mode in (0, 1) and mflups > 0
+    i = b.info
+    assert (i.variant, i.block_size, i.nodes_per_thread, i.round_mode) == (v, bs, npt, mode)
+    assert all(b.slot_info(s)[2] == 0 for s in slots)
+    b.round(6)
+    for s, (p, om, g) in zip(slots, packs):
+        ref, _ = _oracle_steps(p, om, g, 6)
+        _, ug = oracle.macroscopics(b.pdfs(s), g)
+        _, uo = oracle.macroscopics(ref, g)
+        assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= 1e-5
+    b.close()
+
+
+@pytest.mark.parametrize("start", ["aa", "et"])
+def test_tuned_variant_equals_fixed(L, start):
+    """A batch whose variant may be tuned is relaid out for both variants
+    while tuning and for the chosen one at the end; afterwards it gives the
+    same bits as a batch built for that variant."""
+    packs = _packs()
+    tun = L.Batch(4 * 16384, variant=start, precision="f32", max_geometries=4, tune_variant=1)
+    ts = [tun.admit(*p) for p in packs]
+    tun.round(3)
+    v, _, _, _, _ = tun.tune(rounds=1, k=2)
+    tun.round(6)
+    fixed = L.Batch(4 * 16384, variant="aa" if v == L.LBM_AA else "et", precision="f32", max_geometries=4)
+    fs = [fixed.admit(*p) for p in packs]
+    fixed.round(6)
+    for a, c in zip(fs, ts):
+        assert np.array_equal(fixed.pdfs(a), tun.pdfs(c))
+    fixed.close()
+    tun.close()
+
+
+def _random_mask(dims, solid_frac, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.random(int(np.prod(dims))) < solid_frac).astype(np.uint8)
+
+
+def _oracle_solve(mask, dims, per, omega, g, k_round=100, tol=1e-6, cap=200000):
+    cells, node_of = oracle.build_nodes(dims, per, mask)
+    idx = oracle.build_idx(dims, per, mask, cells, node_of)
+    f = oracle.rest_state(cells.size)
+    prev, steps = None, 0
+    while steps < cap:
+        _, phi = oracle.flux(f, g)  # state at the start of the round
+        f = oracle.run_sparse(idx, f, k_round, omega, g)
+        steps += k_round
+        if prev is not None and abs(phi - prev) < tol * abs(phi):
+            break
+        prev = phi
+    return oracle.permeability(phi, int(np.prod(dims)), omega, g[0]), steps
+
+
+@pytest.mark.parametrize("variant,precision,tol_k", [("aa", "f64", 1e-10), ("et", "f32", 1e-5),
+                                                     ("aa", "f16s", 1e-3)])
+def test_mask_admission_steady_flux_and_permeability(L, variant, precision, tol_k):
+    """A random (not sphere) solid mask admitted through lbm_batch_admit,
+    beside a sphere pack: the library's steady-flux test stops it where the
+    oracle's rule does, and its permeability matches the oracle's."""
+    dims, per, omega, g = (18, 14, 12), (1, 1, 1), 1.0, (1e-5, 0.0, 0.0)
+    mask = _random_mask(dims, 0.25, 41)
+    k_ora, steps_ora = _oracle_solve(mask, dims, per, omega, g)
+    b = L.Batch(4 * 16384, variant=variant, precision=precision, max_geometries=4,
+                f16_scale=2.0 ** 20 if precision == "f16s" else 0.0)
+    s = b.admit_mask(mask, dims, per, omega, g, tol=1e-6, max_steps=100000)
+    other = b.admit(*_packs()[0], tol=1e-6)
+    assert b.slot_info(s)[0] == int((mask == 0).sum())
+    done = 0
+    while not done:
+        b.round(100)
+        done, k, steps = b.poll(s)
+    assert done == 1
+    if precision != "f16s":
+        assert steps == steps_ora
+    assert abs(k - k_ora) <= tol_k * k_ora, (k, k_ora)
+    assert b.poll(other)[2] == steps
+    b.close()
+
+
+def test_step_cap_and_release_from_poll(L):
+    b = L.Batch(2 * 16384, variant="aa", precision="f32", max_geometries=4)
+    p, om, g = _packs()[0]
+    s = b.admit(p, om, g, tol=0.0, max_steps=300)  # tol 0: never steady
+    states = []
+    for _ in range(3):
+        b.round(100)
+        states.append(b.poll(s))
+    assert [d for d, _, _ in states] == [0, 0, 2] and states[-1][2] == 300
+    assert np.isfinite(states[-1][1]) and states[-1][1] > 0
+    zero_g = b.admit(p, om, (0.0, 0.0, 0.0), tol=1e-6)
     b.round(2)
+    assert np.isnan(b.poll(zero_g)[1])
     b.close()
 
 
@@ -139,7 +240,7 @@ def test_folded_and_plain_idx_agree(L, precision):
         slots = [b.admit(p, om, g) for p, om, g in _packs()]
         b.round(5)
         b.round(3)
-        outs.append([b.pdfs(s) for s in slots] + [b.poll(s) for s in slots])
+        outs.append([b.pdfs(s) for s in slots] + [b.flux(s) for s in slots])
         b.close()
     for a, c in zip(outs[0], outs[1]):
         if isinstance(a, np.ndarray):

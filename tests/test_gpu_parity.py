@@ -290,45 +290,6 @@ def test_compressed_grid_shifts(lbm, shift, per):
     lat.close()
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
-@pytest.mark.parametrize("nx", [2, 6, 64, 66, 130])
-@pytest.mark.parametrize("per", [(1, 1, 1), (1, 0, 1), (1, 1, 0)])
-def test_aa_x_pairs_match_oracle(lbm, precision, nx, per):
-    """AA pattern with two x-adjacent nodes per thread (periodic x, even nx,
-    no solid cells): rows of one pair, of partial warps and of several warps;
-    walls on y or z; 6 steps against the oracle."""
-    dims = (nx, 5, 4)
-    _, f0 = _case(dims, 0.0, seed=nx)
-    g = (2e-5, 1e-5, -1e-5)
-    ref = oracle.run_push(dims, per, None, f0, 6, 1.3, g)
-    lat = _lattice(lbm, dims, per, "aa", precision=precision, omega=1.3, force=g, pair_x=1)
-    lat.set_geometry(None)
-    lat.set_pdfs(f0)
-    m0, j0 = oracle.flux(f0, g)
-    m, j = lat.step_flux(6)
-    # fused sums: per-node moments in the storage's arithmetic, summed in FP64
-    assert abs(m - m0) <= (1e-12 if precision == "f64" else 1e-6) * m0
-    out = lat.pdfs()
-    _compare(precision, out, ref, g, slice(None))
-    lat.close()
-
-
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
-@pytest.mark.parametrize("nx", [2, 64, 66])
-def test_aa_x_pairs_streaming_exact(lbm, precision, nx):
-    dims, per = (nx, 6, 3), (1, 0, 1)
-    n = int(np.prod(dims))
-    scale = 2.0 ** 20
-    f0 = _dyadic_state(n, scale, 9)
-    ref = oracle.run_push(dims, per, None, f0, 4, 0.0)
-    lat = _lattice(lbm, dims, per, "aa", precision=precision, omega=0.0, f16_scale=scale, pair_x=1)
-    lat.set_geometry(None)
-    lat.set_pdfs(f0)
-    lat.step(4)
-    assert np.array_equal(lat.pdfs(), ref)
-    lat.close()
-
-
 @pytest.mark.parametrize("slab", [1, 7, 100, 0])
 @pytest.mark.parametrize("per", [(1, 1, 1), (1, 1, 0), (0, 1, 1)])
 def test_compressed_grid_node_list_slabs(lbm, slab, per):

@@ -45,7 +45,7 @@ def test_permeability_matches_oracle(pack_and_oracle, variant, precision):
                       omega=OMEGA, force=(GX, 0, 0))
     lat.set_geometry_spheres(pack.centres, pack.radius, pack.unit)
     lat.init()
-    res = permeability.solve(lat, OMEGA, GX)
+    res = permeability.solve(lat)
     lat.close()
     assert res.converged
     assert abs(res.k - k_ora) <= TOL_K[precision] * k_ora, (res.k, k_ora)

@@ -49,11 +49,15 @@ def test_gpu_model_values():
 
 
 def test_fp64_pipe_roof():
-    from paper_1111_0922_gb300 import model
-
-    # 2 FP64 instructions per clock per SM x 152 SMs x 2.07 GHz / 127 per update
-    assert abs(model.fp64_roof_mflups() - 2 * 152 * 2.07e9 / 127 / 1e6) < 1e-6
-    assert model.fp64_inst_per_flup(True, True) == 127 + 16 + 18
-    bound, roof = model.bound_roof("aa", False, "f64", 6780.0)
-    assert bound == "alu" and roof < model.roof_mflups("aa", False, "f64", 6780.0)
-    assert model.bound_roof("aa", False, "f32", 6780.0)[0] == "hbm"
+    # every input is a parameter: 152 SMs x 2 instructions per clock x 2 GHz
+    pipe = model.Fp64Pipe(152, 2.0, 2.0, {"bgk": 100.0, "bgk_force": 110.0, "trt_force": 130.0})
+    assert abs(pipe.inst_rate() - 608e9) < 1.0
+    assert abs(pipe.roof_mflups() - 6080.0) < 1e-6
+    assert abs(pipe.roof_mflups(force=True, trt=True) - 608e3 / 130.0) < 1e-6
+    bound, roof = model.bound_roof("aa", False, "f64", 6780.0, pipe)
+    assert bound == "alu" and roof == pipe.roof_mflups()
+    # the two-step scheme adds its stream kernel's HBM time
+    b2, r2 = model.bound_roof("ts", False, "f64", 6780.0, pipe)
+    assert b2 == "alu" and r2 < roof
+    assert model.bound_roof("aa", False, "f32", 6780.0, pipe)[0] == "hbm"
+    assert model.bound_roof("aa", False, "f64", 6780.0)[0] == "hbm"

@@ -12,7 +12,9 @@ from paper_1111_0922_gb300 import serving
 
 class OracleEngine:
     """Same interface as serving.BatchEngine; capacity in fluid nodes;
-    a round costs `nodes * k / rate` simulated seconds."""
+    a round costs `nodes * k / rate` simulated seconds.  Like the library,
+    it decides convergence itself (relative flux change between rounds) and
+    reports the permeability from the oracle's flux."""
 
     def __init__(self, capacity, clock, rate=2e5):
         self.capacity, self.clock, self.rate = capacity, clock, rate
@@ -21,7 +23,7 @@ class OracleEngine:
         self.max_used = 0
         self.order = []
 
-    def admit(self, req):
+    def admit(self, req, tol, max_steps):
         p = req.pack
         mask = oracle.sphere_mask(p.dims, p.periodic, p.centres, p.radius, p.unit)
         cells, node_of = oracle.build_nodes(p.dims, p.periodic, mask)
@@ -30,7 +32,8 @@ class OracleEngine:
             raise serving.OutOfCapacity("full")
         idx = oracle.build_idx(p.dims, p.periodic, mask, cells, node_of)
         slot = min(set(range(len(self.slots) + 1)) - set(self.slots))
-        self.slots[slot] = dict(req=req, idx=idx, f=oracle.rest_state(n), steps=0, flux=0.0, mass=0.0)
+        self.slots[slot] = dict(req=req, idx=idx, f=oracle.rest_state(n), steps=0, flux=0.0, prev=None, done=0,
+                                tol=tol, max_steps=max_steps, pending=False)
         self.used += n
         self.max_used = max(self.max_used, self.used)
         self.order.append(req.rid)
@@ -44,15 +47,23 @@ class OracleEngine:
         total = 0
         for s in self.slots.values():
             r = s["req"]
-            s["mass"], s["flux"] = oracle.flux(s["f"], r.force)
+            _, s["flux"] = oracle.flux(s["f"], r.force)
             s["f"] = oracle.run_sparse(s["idx"], s["f"], k, r.omega, r.force, nthreads=1)
             s["steps"] += k
+            s["pending"] = True
             total += s["idx"].shape[1]
         self.clock.advance(total * k / self.rate)
 
     def poll(self, slot):
         s = self.slots[slot]
-        return s["mass"], s["flux"], s["steps"]
+        if s["pending"] and not s["done"]:
+            steady = s["prev"] is not None and abs(s["flux"] - s["prev"]) < s["tol"] * abs(s["flux"])
+            s["prev"] = s["flux"]
+            s["done"] = 1 if steady else (2 if s["steps"] >= s["max_steps"] else 0)
+        s["pending"] = False
+        r = s["req"]
+        k = oracle.permeability(s["flux"], int(np.prod(r.pack.dims)), r.omega, r.force[0])
+        return s["done"], k, s["steps"]
 
 
 def _requests(n=5, rate=50.0):
