@@ -94,9 +94,11 @@ def profile_records():
 def profiled_traffic(kernel_key, precision):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or
     None when the kernel sources changed since the capture."""
+    want = kernel_source_hash(precision)
     for p in profile_records():
-        if len(p) == 5 and p[0] == "dram_bytes_per_launch" and p[1] == kernel_key and p[3] == "source_hash":
-            return float(p[2]) if p[4] == kernel_source_hash(precision) else None
+        if len(p) == 5 and p[0] == "dram_bytes_per_launch" and p[1] == kernel_key and p[3] == "source_hash" \
+                and p[4] == want:
+            return float(p[2])
     return None
 
 
@@ -551,9 +553,12 @@ def run_serving(torch, lbm, args):
     """Poisson arrivals (20 requests/s, seed 5) of sphere packs with sides
     U{64..384} and porosity U[0.3, 0.8), r = 8, served by continuous batching
     with FP16-stored PDFs (FP32 collision, FP64 flux sums) within a 150 GB HBM
-    budget; then the same requests' smallest few (by fluid nodes, named in
-    the output) solved one at a time with FP64 storage and arithmetic, for a
-    like-for-like comparison of service time and permeability."""
+    budget.  Then a like-for-like comparison on a matched subset of the same
+    trace (evenly spaced request ids, with their arrival times): served by
+    the FP16 batch alone, and by the FP64 single-solve path one request at a
+    time (each solve starts when the request has arrived and the previous
+    solve is done).  Both report solves/s and latency over the same
+    requests, and the permeability error of FP16 against FP64."""
     from paper_1111_0922_gb300 import permeability, serving
 
     budget = 150e9
@@ -561,42 +566,59 @@ def run_serving(torch, lbm, args):
     cap = min(int(budget / per_slot), (1 << 31) - 65536)
     reqs = serving.poisson_requests(args.serve_requests, 20.0, seed=5)
     offered = sum(int(r.pack.dims[0] ** 3 * r.pack.porosity_target) for r in reqs) / (reqs[-1].arrival or 1.0)
-    eng = serving.BatchEngine(cap, variant="aa", precision="f16s", f16_scale=2.0 ** 26,
-                              max_geometries=len(reqs) + 1)
-    st = serving.serve(reqs, eng, serving.RealClock(), k_round=100, tol=1e-6, max_steps=args.serve_max_steps)
-    eng.close()
-    torch.cuda.empty_cache()
+
+    def fp16_serve(trace):
+        eng = serving.BatchEngine(cap, variant="aa", precision="f16s", f16_scale=2.0 ** 26,
+                                  max_geometries=len(trace) + 1)
+        st = serving.serve(trace, eng, serving.RealClock(), k_round=100, tol=1e-6, max_steps=args.serve_max_steps)
+        eng.close()
+        torch.cuda.empty_cache()
+        return st
+
+    st = fp16_serve(reqs)
     summ = st.summary()
-    by_id = {x.rid: x for x in st.results}
-    # the matched subset: the requests with the fewest fluid nodes
-    served = sorted((x for x in st.results if x.nodes > 0), key=lambda x: x.nodes)
-    subset = [x.rid for x in served[: args.serve_fp64]]
+    # matched subset: every (n / m)-th request, with its arrival time
+    m = max(1, min(args.serve_fp64, len(reqs)))
+    subset = [reqs[i * len(reqs) // m] for i in range(m)]
+    t0 = subset[0].arrival
+    sub_trace = [serving.Request(r.rid, r.arrival - t0, r.pack, r.omega, r.force) for r in subset]
+    sub16 = fp16_serve(sub_trace)
+    by16 = {x.rid: x for x in sub16.results}
+    # FP64, one solve at a time in arrival order
+    clock = 0.0
     base = []
-    for rid in subset:
-        r = reqs[rid]
+    for r in sub_trace:
+        start = max(clock, r.arrival)
         lat = lbm.Lattice(r.pack.dims, r.pack.periodic, variant="aa", addressing="indirect", precision="f64",
                           omega=r.omega, force=r.force)
-        t0 = time.perf_counter()
+        t1 = time.perf_counter()
         lat.set_geometry_spheres(r.pack.centres, r.pack.radius, r.pack.unit)
         lat.init()
         res = permeability.solve(lat, 100, 1e-6, max_steps=args.serve_max_steps)
-        base.append((rid, res.k, time.perf_counter() - t0, res.steps, res.converged))
+        service = time.perf_counter() - t1
         lat.close()
         torch.cuda.empty_cache()
-    k_err = {rid: abs(by_id[rid].k - k) / k for rid, k, _, _, _ in base if by_id[rid].converged}
-    fp16_service = [by_id[rid].finished - by_id[rid].admitted for rid in subset]
+        clock = start + service
+        base.append((r.rid, res.k, service, res.steps, res.converged, clock - r.arrival, clock))
+    lat64 = np.array([b[5] for b in base])
+    k_err = {rid: abs(by16[rid].k - k) / k for rid, k, _, _, _, _, _ in base if by16[rid].converged}
+    s16 = sub16.summary()
     return {"workload": "Poisson 20/s (seed 5), %d requests, side U{64..384}, porosity U[0.3,0.8), r = 8, "
                         "AA pattern, FP16 storage (S = 2^26), 150 GB budget" % len(reqs),
             "offered_node_rate_per_s": round(offered, 1), "capacity_slots": cap,
             **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()},
             "matched_subset": {
-                "request_ids": subset, "fluid_nodes": [by_id[rid].nodes for rid in subset],
-                "fp64_one_at_a_time": {
-                    "service_s": [round(b[2], 3) for b in base], "steps": [b[3] for b in base],
-                    "solves_per_s": round(len(base) / sum(b[2] for b in base), 4) if base else None},
-                "fp16_batched": {
-                    "service_s": [round(t, 3) for t in fp16_service], "steps": [by_id[rid].steps for rid in subset],
-                    "latency_s": [round(by_id[rid].latency, 3) for rid in subset]},
+                "request_ids": [r.rid for r in subset],
+                "fluid_nodes": [by16[r.rid].nodes for r in subset],
+                "fp16_batched": {"solves_per_s": round(s16["solves_per_s"], 4),
+                                 "p50_latency_s": round(s16["p50_latency_s"], 3),
+                                 "p99_latency_s": round(s16["p99_latency_s"], 3),
+                                 "steps": [by16[r.rid].steps for r in subset]},
+                "fp64_one_at_a_time": {"solves_per_s": round(len(base) / (base[-1][6] - sub_trace[0].arrival), 4),
+                                       "p50_latency_s": round(float(np.percentile(lat64, 50)), 3),
+                                       "p99_latency_s": round(float(np.percentile(lat64, 99)), 3),
+                                       "service_s": [round(b[2], 3) for b in base], "steps": [b[3] for b in base],
+                                       "converged": all(b[4] for b in base)},
                 "k_rel_err_fp16_vs_fp64": {str(r): float("%.3g" % e) for r, e in k_err.items()},
                 "k_rel_err_max": max(k_err.values()) if k_err else None}}
 
