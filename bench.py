@@ -563,13 +563,17 @@ def run_serving(torch, lbm, args):
 
     budget = 150e9
     per_slot = lbm.lbm_batch_bytes_per_slot(lbm.LBM_AA, lbm.LBM_F16S)
-    cap = min(int(budget / per_slot), (1 << 31) - 65536)
+    # below 2^30 slots (118 GB of the budget; the whole trace needs about
+    # 0.6e9) the AA pattern's IDX holds the bounce-back slots, no branch per link
+    cap = min(int(budget / per_slot), (1 << 30) - 8192)
     reqs = serving.poisson_requests(args.serve_requests, 20.0, seed=5)
     offered = sum(int(r.pack.dims[0] ** 3 * r.pack.porosity_target) for r in reqs) / (reqs[-1].arrival or 1.0)
 
     def fp16_serve(trace):
+        # launch shape chosen by lbm_batch_tune on the 64-pack FP16 batch:
+        # AA pattern, 512 threads x 4 nodes, per-step launches
         eng = serving.BatchEngine(cap, variant="aa", precision="f16s", f16_scale=2.0 ** 26,
-                                  max_geometries=len(trace) + 1)
+                                  max_geometries=len(trace) + 1, block_size=512, nodes_per_thread=4)
         st = serving.serve(trace, eng, serving.RealClock(), k_round=100, tol=1e-6, max_steps=args.serve_max_steps)
         eng.close()
         torch.cuda.empty_cache()
