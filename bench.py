@@ -75,14 +75,14 @@ def kernel_source_hash(precision="f32"):
     return h.hexdigest()[:16]
 
 
-def profile_records():
+def profile_records(directory=None):
     """Machine-readable lines of the committed ncu summaries (profiles/*.md):
       dram_bytes_per_launch <key> <bytes> source_hash <hash>
       fp64_inst_per_flup <collision kind> <count> source_hash <hash>
       fp64_inst_per_clk_sm <peak>
     returned as lists of fields."""
     recs = []
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+    for path in sorted(glob.glob(os.path.join(directory or os.path.join(ROOT, "profiles"), "*.md"))):
         with open(path) as f:
             for line in f:
                 parts = line.split()
@@ -91,24 +91,24 @@ def profile_records():
     return recs
 
 
-def profiled_traffic(kernel_key, precision):
+def profiled_traffic(kernel_key, precision, directory=None):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or
     None when the kernel sources changed since the capture."""
     want = kernel_source_hash(precision)
-    for p in profile_records():
+    for p in profile_records(directory):
         if len(p) == 5 and p[0] == "dram_bytes_per_launch" and p[1] == kernel_key and p[3] == "source_hash" \
                 and p[4] == want:
             return float(p[2])
     return None
 
 
-def profiled_fp64():
+def profiled_fp64(directory=None):
     """(FP64 thread instructions per SM clock, {collision kind: FP64 thread
     instructions per update}) from the committed ncu capture; a count whose
     kernel sources changed since the capture is left out."""
     per_clk = None
     per_flup = {}
-    for p in profile_records():
+    for p in profile_records(directory):
         if p[0] == "fp64_inst_per_clk_sm" and len(p) == 2:
             per_clk = float(p[1])
         elif p[0] == "fp64_inst_per_flup" and len(p) == 5 and p[4] == kernel_source_hash("f64"):
