@@ -109,8 +109,6 @@ typedef struct lbm_config {
                                 pass, links to tiles of earlier colours completed in place;
                                 2 = the same with each tile staged by one tensor copy (TMA) in
                                 persistent blocks (SoA, row pitch a multiple of 16 bytes);
-                                3 = two passes per step: every tile collides and completes its own
-                                links, then one pass completes the links between tiles;
                                 0 = default: 1 (measured fastest on GB300) */
   int32_t pair_z;            /* Cell pairs, LBM_F16S or LBM_F32 storage, SoA, full grid without
                                 solid cells: LBM_AA, LBM_TS, LBM_OS_PUSH / PULL

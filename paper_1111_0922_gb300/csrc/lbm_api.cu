@@ -57,9 +57,9 @@ struct lbm {
   alignas(64) CUtensorMap swap_map{};
   bool swap_tma = false;
   int nsm = 0;
-  // swap on a full grid: per-tile link-class tables (coloured and two-pass)
-  uint16_t *d_swap_tcls = nullptr, *d_swap_tcls_all = nullptr;
-  uint32_t *d_swap_tables = nullptr, *d_swap_tables_all = nullptr;
+  // swap on a full grid: per-tile link-class tables of the coloured passes
+  uint16_t *d_swap_tcls = nullptr;
+  uint32_t *d_swap_tables = nullptr;
 };
 
 static std::string g_last_error;
@@ -323,8 +323,6 @@ static SwapTiles swap_tiles(const lbm_t *h) {
   t.ncolours = swap_colours(t, h->cfg.periodic[0], h->cfg.periodic[1], h->cfg.periodic[2]);
   t.tcls = h->d_swap_tcls;
   t.tables = h->d_swap_tables;
-  t.tcls_all = h->d_swap_tcls_all;
-  t.tables_all = h->d_swap_tables_all;
   return t;
 }
 
@@ -408,8 +406,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_t **out) {
   if (cfg->store_hint != 0 && cfg->store_hint != 1) return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint must be 0 or 1");
   if (cfg->store_hint == 1 && (!(cfg->variant == LBM_OS_PUSH || cfg->variant == LBM_OS_PULL) || cfg->layout != LBM_SOA))
     return fail(nullptr, LBM_ERR_INVALID_ARG, "store_hint = 1 needs LBM_OS_PUSH or LBM_OS_PULL with LBM_SOA");
-  if (cfg->swap_schedule < 0 || cfg->swap_schedule > 3)
-    return fail(nullptr, LBM_ERR_INVALID_ARG, "swap_schedule must be 0 .. 3");
+  if (cfg->swap_schedule < 0 || cfg->swap_schedule > 2)
+    return fail(nullptr, LBM_ERR_INVALID_ARG, "swap_schedule must be 0 .. 2");
 
   lbm_t *h = new lbm_t();
   h->cfg = *cfg;
@@ -630,10 +628,10 @@ static lbm_status build_geometry(lbm_t *h) {
   }
   if (c.variant == LBM_SWAP && !ind) {
     const SwapTiles t = swap_tiles(h);
-    for (int all = 0; all < 2; ++all) {
+    {
       std::vector<uint16_t> tcls;
       std::vector<uint32_t> tables;
-      build_swap_tables(t, c.periodic, all == 1, tcls, tables);
+      build_swap_tables(t, c.periodic, tcls, tables);
       uint16_t *dt = static_cast<uint16_t *>(dalloc(h, sizeof(uint16_t) * tcls.size(), h->geo_allocs));
       uint32_t *dtab = static_cast<uint32_t *>(dalloc(h, sizeof(uint32_t) * tables.size(), h->geo_allocs));
       if (!dt || !dtab) return fail(h, LBM_ERR_OOM, "swap link-class tables");
@@ -641,8 +639,8 @@ static lbm_status build_geometry(lbm_t *h) {
       CUDA_TRY(h, cudaMemcpyAsync(dtab, tables.data(), sizeof(uint32_t) * tables.size(), cudaMemcpyHostToDevice,
                                   h->stream));
       CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
-      (all ? h->d_swap_tcls_all : h->d_swap_tcls) = dt;
-      (all ? h->d_swap_tables_all : h->d_swap_tables) = dtab;
+      h->d_swap_tcls = dt;
+      h->d_swap_tables = dtab;
     }
   }
   // reduction partials: enough for a step launch and for the read-out kernel
@@ -676,8 +674,8 @@ static void reset_geometry(lbm_t *h) {
   h->nodes = h->nghost = h->nn = h->slots = h->npad = h->ipad = 0;
   h->idx_folded = false;
   h->swap_tma = false;
-  h->d_swap_tcls = h->d_swap_tcls_all = nullptr;
-  h->d_swap_tables = h->d_swap_tables_all = nullptr;
+  h->d_swap_tcls = nullptr;
+  h->d_swap_tables = nullptr;
   h->steps = 0;
   for (int i = 0; i < Q; ++i) h->map[i] = i;
 }
@@ -798,7 +796,7 @@ static int kernels_per_step(const lbm_t *h) {
       return (h->cfg.nz + slab - 1) / slab + (h->cfg.periodic[2] ? 1 : 0);
     }
     case LBM_SWAP:
-      return (h->cfg.addressing == LBM_INDIRECT || h->cfg.swap_schedule == 3) ? 2 : swap_tiles(h).ncolours;
+      return h->cfg.addressing == LBM_INDIRECT ? 2 : swap_tiles(h).ncolours;
     default: return 1;
   }
 }
@@ -1079,13 +1077,6 @@ static lbm_status swap_step(lbm_t *h, bool red, int *red_blocks) {
     return LBM_OK;
   }
   SwapTiles t = swap_tiles(h);
-  if (h->cfg.swap_schedule == 3) {
-    const LaunchShape L = shape_of(h);
-    p.partials = h->d_partials;
-    launch_swap_two_pass(p, t, k, L.grid, L.block, h->stream);
-    if (red_blocks) *red_blocks = t.ntx * t.nty * t.ntz;
-    return LBM_OK;
-  }
   if (t.pairs) {
     // the swap runs on the grid of pair words: nz/2 planes, npad/2 words
     p.g.nz = h->cfg.nz / 2;

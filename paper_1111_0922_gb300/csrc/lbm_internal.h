@@ -79,19 +79,14 @@ struct SwapTiles {
   // index of its table; a table is 2 + 3 x 18 words: the earlier-colour and
   // self neighbour masks of the 27 tile offsets, then for each of the 18
   // cell classes of a full tile the outside / remote / self link masks.
-  // *_all: the same for the two-pass schedule (no tile counts as earlier).
-  const uint16_t *tcls = nullptr, *tcls_all = nullptr;
-  const uint32_t *tables = nullptr, *tables_all = nullptr;
+  const uint16_t *tcls = nullptr;
+  const uint32_t *tables = nullptr;
   int pairs = 0;  // tiles of the grid of cell-pair words (Grid::zpair)
 };
 constexpr int kSwapTableWords = 2 + 3 * 18;
-void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, std::vector<uint16_t> &tcls,
+void build_swap_tables(const SwapTiles &t, const int per[3], std::vector<uint16_t> &tcls,
                        std::vector<uint32_t> &tables);
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s);
-// two-pass schedule: all tiles (own links), then the links between tiles
-// (one thread per cell on face_grid x face_block, z planes strided by grid z)
-void launch_swap_two_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, dim3 face_grid, dim3 face_block,
-                          cudaStream_t s);
 // the same pass with tensor-copy staging (full grid, SoA, strides multiple of
 // 16 bytes); `map` describes the lattice as a 4D tensor (x, y, z, array) with
 // the tile as its box.  Launches persistent blocks (as many as are resident

@@ -21,9 +21,6 @@ extern template void swap_pass_pair_t<CodecPair<CodecF32>>(const StepParams &, c
                                                            size_t, cudaStream_t);
 extern template void swap_pass_pair_t<CodecPair<CodecF16S>>(const StepParams &, const SwapPass &, const KernelKey &,
                                                             size_t, cudaStream_t);
-extern template void swap_faces_t<CodecF64>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
-extern template void swap_faces_t<CodecF32>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
-extern template void swap_faces_t<CodecF16S>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
 extern template int swap_pass_tma_t<CodecF64>(const StepParams &, const SwapPass &, const KernelKey &,
                                               const CUtensorMap *, int, int, cudaStream_t);
 extern template int swap_pass_tma_t<CodecF32>(const StepParams &, const SwapPass &, const KernelKey &,
@@ -53,7 +50,7 @@ static int axis_colour_host(int t, int nt, int periodic) {
   return t & 1;
 }
 
-void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, std::vector<uint16_t> &tcls,
+void build_swap_tables(const SwapTiles &t, const int per[3], std::vector<uint16_t> &tcls,
                        std::vector<uint32_t> &tables) {
   auto ncol = [](int nt, int periodic) { return nt == 1 ? 1 : ((periodic && (nt & 1)) ? 3 : 2); };
   const int nt[3] = {t.ntx, t.nty, t.ntz};
@@ -86,7 +83,7 @@ void build_swap_tables(const SwapTiles &t, const int per[3], bool none_earlier, 
           if (!exists) continue;
           if (self)
             sm |= 1u << l;
-          else if (!none_earlier && colour(nb) < own)
+          else if (colour(nb) < own)
             em |= 1u << l;
         }
         auto key = std::make_pair(em, sm);
@@ -179,33 +176,6 @@ static SwapPass pass_of(const StepParams &p, const SwapTiles &t) {
   sp.tcls = t.tcls;
   sp.tables = t.tables;
   return sp;
-}
-
-// Two-pass schedule (see k_swap_faces): first every tile in one launch,
-// completing only its own links (colour 0 for all, so no neighbour counts as
-// earlier), then the pass over the links between tiles.
-void launch_swap_two_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, dim3 face_grid, dim3 face_block,
-                          cudaStream_t s) {
-  SwapPass sp = pass_of(p, t);
-  sp.colour = 0;
-  sp.start[0] = sp.start[1] = sp.start[2] = 0;
-  sp.count[0] = t.ntx;
-  sp.count[1] = t.nty;
-  sp.count[2] = t.ntz;
-  sp.stride = 1;
-  sp.tcls = t.tcls_all;
-  sp.tables = t.tables_all;
-  const size_t smem = swap_smem_bytes(t, k.precision);
-  if (k.precision == 0) {
-    swap_pass_t<CodecF64>(p, sp, k, smem, s);
-    swap_faces_t<CodecF64>(p, sp, k.aos, face_grid, face_block, s);
-  } else if (k.precision == 1) {
-    swap_pass_t<CodecF32>(p, sp, k, smem, s);
-    swap_faces_t<CodecF32>(p, sp, k.aos, face_grid, face_block, s);
-  } else {
-    swap_pass_t<CodecF16S>(p, sp, k, smem, s);
-    swap_faces_t<CodecF16S>(p, sp, k.aos, face_grid, face_block, s);
-  }
 }
 
 void launch_swap_pass(const StepParams &p, const SwapTiles &t, const KernelKey &k, cudaStream_t s) {

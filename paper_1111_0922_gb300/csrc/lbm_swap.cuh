@@ -447,76 +447,11 @@ struct LaunchSwapTma {
   }
 };
 
-// Two-phase schedule, second pass: every link between two different tiles
-// (the first pass collided every tile and completed only its own links,
-// leaving each inter-tile link reversed at both ends) is completed by
-// exchanging slot opp(i) of x with slot i of x + c_i.  The link belongs to
-// its end x with the odd direction i, so each is exchanged once; a link to a
-// wall or a solid cell has nothing to exchange, and a link that wraps onto
-// the same tile across a periodic face was completed in the first pass.
-// Raw storage values are moved (no decoding).
-template <class C, int AOS>
-__global__ void __launch_bounds__(256) k_swap_faces(StepParams p, SwapPass sp) {
-  using S = typename C::S;
-  S *A = static_cast<S *>(p.A);
-  const Grid &g = p.g;
-  auto at = [&](int k, int slot) -> S & { return AOS ? A[(int64_t)slot * Q + k] : A[(int64_t)k * p.npad + slot]; };
-  for (int z = blockIdx.z; z < g.nz; z += gridDim.z) {
-    DirectNode nd;
-    nd.x = blockIdx.x * blockDim.x + threadIdx.x;
-    nd.y = blockIdx.y * blockDim.y + threadIdx.y;
-    nd.z = z;
-    if (nd.x >= g.nx || nd.y >= g.ny || !nd.setup(g)) continue;
-    const int own[3] = {nd.x / sp.tx, nd.y / sp.ty, nd.z / sp.tz};
-    int other[Q];
-    S va[Q], vb[Q];
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      other[i] = -1;
-      const int c[3] = {CX(i), CY(i), CZ(i)};
-      const int n[3] = {g.nx, g.ny, g.nz};
-      const int xyz[3] = {nd.x, nd.y, nd.z};
-      const int t[3] = {sp.tx, sp.ty, sp.tz};
-      bool inter = false;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int v = xyz[a] + c[a];
-        if (v < 0) v += n[a];
-        if (v >= n[a]) v -= n[a];
-        inter = inter || (v / t[a] != own[a]);
-      }
-      if (!inter) continue;
-      const int y = nd.nb(p, i);  // -1 across a wall or into a solid cell
-      if (y < 0) continue;
-      other[i] = y;
-      va[i] = at(OPP(i), nd.s);
-      vb[i] = at(i, y);
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      if (other[i] < 0) continue;
-      at(OPP(i), nd.s) = vb[i];
-      at(i, other[i]) = va[i];
-    }
-  }
-}
-
-template <class C, int AOS, bool IND, bool FORCE, bool RED>
-struct LaunchSwapFaces {
-  static void run(const StepParams &p, const SwapPass &sp, dim3 grid, dim3 block, cudaStream_t s) {
-    if constexpr (!FORCE && !RED && !IND) k_swap_faces<C, AOS><<<grid, block, 0, s>>>(p, sp);
-  }
-};
-
 // Per-precision entry points (instantiated in lbm_swap_<precision>.cu).
 template <class C>
 void swap_pass_t(const StepParams &p, const SwapPass &sp, const KernelKey &k, size_t smem, cudaStream_t s) {
   const dim3 blocks(sp.count[0], sp.count[1], sp.count[2]);
   dispatch_layout<LaunchSwap, C>(k.aos, false, k.force, k.red, p, sp, smem, blocks, s);
-}
-template <class C>
-void swap_faces_t(const StepParams &p, const SwapPass &sp, int aos, dim3 grid, dim3 block, cudaStream_t s) {
-  dispatch_layout<LaunchSwapFaces, C>(aos, false, false, false, p, sp, grid, block, s);
 }
 // Cell pairs: SoA, full grid only, so only those instantiations.
 template <class C>

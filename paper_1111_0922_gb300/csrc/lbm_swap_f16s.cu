@@ -6,7 +6,6 @@ namespace lbmk {
 template void swap_pass_t<CodecF16S>(const StepParams &, const SwapPass &, const KernelKey &, size_t, cudaStream_t);
 template int swap_pass_tma_t<CodecF16S>(const StepParams &, const SwapPass &, const KernelKey &, const CUtensorMap *,
                                      int, int, cudaStream_t);
-template void swap_faces_t<CodecF16S>(const StepParams &, const SwapPass &, int, dim3, dim3, cudaStream_t);
 template void swap_pass_pair_t<CodecPair<CodecF16S>>(const StepParams &, const SwapPass &, const KernelKey &, size_t,
                                                      cudaStream_t);
 }  // namespace lbmk

@@ -91,7 +91,7 @@ def main(argv=None):
     ap.add_argument("--store-hint", type=int, default=0,
                     help="OS push/pull, SoA: 1 = cache-streaming stores of the second lattice (OS-NT analogue)")
     ap.add_argument("--swap-schedule", type=int, default=0,
-                    help="swap, full grid: 0 default, 1 coloured passes, 2 coloured with tensor-copy staging, 3 two passes")
+                    help="swap, full grid: 0 default, 1 coloured passes, 2 coloured with tensor-copy staging")
     ap.add_argument("--pair-z", type=int, default=0,
                     help="AA, FP16 storage, full grid: 0 default (z pairs where allowed), 2 one node per thread")
     ap.add_argument("--trt", action="store_true", help="two-relaxation-time collision, magic 3/16")

@@ -90,7 +90,7 @@ def test_host_only_calls(lib):
             lbm.lbm_create(bad)
         assert e.value.status == lbm.LBM_ERR_INVALID_ARG
     bad = lbm.lbm_config_default()
-    bad.swap_schedule = 4
+    bad.swap_schedule = 3
     with pytest.raises(lbm.LBMError):
         lbm.lbm_create(bad)
     bad = lbm.lbm_config_default()

@@ -48,10 +48,8 @@ def test_staged_swap_equals_plain_and_oracle(L, precision, dims, per):
     g = (2e-5, 1e-5, -5e-6)
     a, sa = _run(L, dims, per, precision, 2, solid, f0, 6, 1.2, g)
     b, sb = _run(L, dims, per, precision, 1, solid, f0, 6, 1.2, g)
-    c, sc = _run(L, dims, per, precision, 3, solid, f0, 6, 1.2, g)
-    assert sa == 1 and sb == 0 and sc == 0
+    assert sa == 1 and sb == 0
     assert np.array_equal(a, b)
-    assert np.array_equal(a, c)  # the same arithmetic per node, exact moves
     ref = oracle.run_push(dims, per, solid, f0, 6, 1.2, g)
     fl = solid == 0
     if precision == "f64":
@@ -87,7 +85,7 @@ def test_bounded_wait_gives_up_and_context_survives(L):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("staging", [0, 1, 2, 3])
+@pytest.mark.parametrize("staging", [0, 1, 2])
 @pytest.mark.parametrize("per", [(1, 1, 1), (1, 0, 1), (0, 0, 0), (0, 1, 1)])
 @pytest.mark.parametrize("dims", [(64, 8, 6), (96, 12, 8), (72, 9, 5), (192, 4, 6), (200, 6, 6)])
 def test_swap_without_solids_matches_oracle(L, dims, per, staging):

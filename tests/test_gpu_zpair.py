@@ -147,7 +147,7 @@ def test_swap_pairs_equal_single_nodes_bitwise(L, dims, per, force, precision):
 
 def test_swap_pairs_only_where_allowed(L):
     for dims, per, kw in (((64, 4, 6), (1, 1, 1), {}), ((64, 4, 8), (1, 1, 0), {}), ((64, 4, 4), (1, 1, 1), {}),
-                          ((64, 4, 8), (1, 1, 1), {"swap_schedule": 2}), ((64, 4, 8), (1, 1, 1), {"swap_schedule": 3})):
+                          ((64, 4, 8), (1, 1, 1), {"swap_schedule": 2})):
         lat = L.Lattice(dims, per, variant="swap", precision="f32", **kw)
         lat.set_geometry(None)
         assert lat.info.pair_z == 0, (dims, per, kw)
