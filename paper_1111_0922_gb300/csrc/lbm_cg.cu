@@ -56,6 +56,7 @@ __device__ __forceinline__ void cg_node(const StepParams &p, Node &nd, const Lat
 // (plus the ghost plane), p.g.zghost is set on a periodic z axis.
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 __global__ void __launch_bounds__(256, C::kMinBlocks) k_cg_slab(StepParams p) {
+  chain_wait();
   Lattice<C, AOS> A{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   const int64_t shift = p.g.sxy * (int64_t)(p.zo_write - p.zo_read);
   double m = 0.0, j = 0.0;
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) k_cg_slab(StepParams p) {
 // raw storage values, all 19 arrays.
 template <class S, int AOS>
 __global__ void k_cg_ghost(S *A, int64_t npad, Grid g, int zo) {
+  chain_wait();
   const int64_t plane = g.sxy;  // storage slots per plane
   const int64_t total = 2 * plane * Q;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -129,6 +131,7 @@ struct YPairNode {
 
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(256, PairWord<C>::kMinBlocks) k_cg_slab_yp(StepParams p) {
+  chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
   const Grid &g = p.g;
@@ -190,10 +193,10 @@ struct LaunchCG {
     q.g.zghost = p.g.pz;
     if (p.g.ypair) {
       if constexpr (kPairable<C> && AOS == 0)
-        k_cg_slab_yp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
+        launch_chained(k_cg_slab_yp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, q);
       return;
     }
-    k_cg_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(q);
+    launch_chained(k_cg_slab<C, AOS, false, FORCE, RED>, L.grid, L.block, 0, L.stream, q);
   }
 };
 
@@ -207,19 +210,19 @@ void launch_cg_ghost(const StepParams &p, int precision, int aos, int zo, cudaSt
   const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
   if (precision == 0) {
     if (aos)
-      k_cg_ghost<double, 1><<<grid, 256, 0, s>>>(static_cast<double *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<double, 1>, grid, 256, 0, s, static_cast<double *>(p.A), p.npad, p.g, zo);
     else
-      k_cg_ghost<double, 0><<<grid, 256, 0, s>>>(static_cast<double *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<double, 0>, grid, 256, 0, s, static_cast<double *>(p.A), p.npad, p.g, zo);
   } else if (precision == 1) {
     if (aos)
-      k_cg_ghost<float, 1><<<grid, 256, 0, s>>>(static_cast<float *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<float, 1>, grid, 256, 0, s, static_cast<float *>(p.A), p.npad, p.g, zo);
     else
-      k_cg_ghost<float, 0><<<grid, 256, 0, s>>>(static_cast<float *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<float, 0>, grid, 256, 0, s, static_cast<float *>(p.A), p.npad, p.g, zo);
   } else {
     if (aos)
-      k_cg_ghost<__half, 1><<<grid, 256, 0, s>>>(static_cast<__half *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<__half, 1>, grid, 256, 0, s, static_cast<__half *>(p.A), p.npad, p.g, zo);
     else
-      k_cg_ghost<__half, 0><<<grid, 256, 0, s>>>(static_cast<__half *>(p.A), p.npad, p.g, zo);
+      launch_chained(k_cg_ghost<__half, 0>, grid, 256, 0, s, static_cast<__half *>(p.A), p.npad, p.g, zo);
   }
 }
 
@@ -282,6 +285,7 @@ void launch_cg_ind_prep(const int32_t *idx, int64_t ipad, const int32_t *cells, 
 // of the current offset.
 template <class S, int AOS>
 __global__ void k_cg_ind_ghost(S *A, int64_t npad, int64_t N, int64_t nfirst, int64_t nlast) {
+  chain_wait();
   const int64_t per = nfirst + nlast;
   const int64_t total = per * Q;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -308,14 +312,14 @@ void launch_cg_ind_ghost(void *A, int64_t npad, int precision, int aos, int64_t 
   if (total == 0) return;
   const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
   if (precision == 0) {
-    if (aos) k_cg_ind_ghost<double, 1><<<grid, 256, 0, s>>>(static_cast<double *>(A), npad, N, nfirst, nlast);
-    else k_cg_ind_ghost<double, 0><<<grid, 256, 0, s>>>(static_cast<double *>(A), npad, N, nfirst, nlast);
+    if (aos) launch_chained(k_cg_ind_ghost<double, 1>, grid, 256, 0, s, static_cast<double *>(A), npad, N, nfirst, nlast);
+    else launch_chained(k_cg_ind_ghost<double, 0>, grid, 256, 0, s, static_cast<double *>(A), npad, N, nfirst, nlast);
   } else if (precision == 1) {
-    if (aos) k_cg_ind_ghost<float, 1><<<grid, 256, 0, s>>>(static_cast<float *>(A), npad, N, nfirst, nlast);
-    else k_cg_ind_ghost<float, 0><<<grid, 256, 0, s>>>(static_cast<float *>(A), npad, N, nfirst, nlast);
+    if (aos) launch_chained(k_cg_ind_ghost<float, 1>, grid, 256, 0, s, static_cast<float *>(A), npad, N, nfirst, nlast);
+    else launch_chained(k_cg_ind_ghost<float, 0>, grid, 256, 0, s, static_cast<float *>(A), npad, N, nfirst, nlast);
   } else {
-    if (aos) k_cg_ind_ghost<__half, 1><<<grid, 256, 0, s>>>(static_cast<__half *>(A), npad, N, nfirst, nlast);
-    else k_cg_ind_ghost<__half, 0><<<grid, 256, 0, s>>>(static_cast<__half *>(A), npad, N, nfirst, nlast);
+    if (aos) launch_chained(k_cg_ind_ghost<__half, 1>, grid, 256, 0, s, static_cast<__half *>(A), npad, N, nfirst, nlast);
+    else launch_chained(k_cg_ind_ghost<__half, 0>, grid, 256, 0, s, static_cast<__half *>(A), npad, N, nfirst, nlast);
   }
 }
 
@@ -324,6 +328,7 @@ void launch_cg_ind_ghost(void *A, int64_t npad, int precision, int aos, int64_t 
 // p.B (new offset).
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 __global__ void __launch_bounds__(256, (step_min_cg<C>())) k_cg_ind_slab(StepParams p) {
+  chain_wait();
   using T = typename C::T;
   Lattice<C, AOS> A{static_cast<typename C::S *>(p.A), p.npad, p.scale, p.inv_scale};
   Lattice<C, AOS> B{static_cast<typename C::S *>(p.B), p.npad, p.scale, p.inv_scale};
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(256, (step_min_cg<C>())) k_cg_ind_slab(StepPar
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchCGInd {
   static void run(const StepParams &p, const LaunchShape &L) {
-    k_cg_ind_slab<C, AOS, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+    launch_chained(k_cg_ind_slab<C, AOS, false, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
   }
 };
 

@@ -66,6 +66,7 @@ __device__ __forceinline__ void run_collision(typename C::T (&d)[Q], const StepP
 // Two-step, kernel 1 (Tab. 1, collision): A -> B at the same slot.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_ts_collide(StepParams p) {
+  chain_wait();
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
@@ -105,6 +106,7 @@ __device__ __forceinline__ void ts_stream_node(const StepParams &p, Node &nd, co
 
 template <class C, int AOS, class Node>
 __global__ void LBM_STEP_BOUNDS k_ts_stream(StepParams p) {
+  chain_wait();
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS>(p.B, p);
   LBM_NODE_LOOP(Node, it) {
@@ -141,6 +143,7 @@ __device__ __forceinline__ void os_push_node(const StepParams &p, Node &nd, cons
 
 template <class C, int AOS, class Node, bool FORCE, bool RED, bool CS>
 __global__ void LBM_STEP_BOUNDS k_os_push(StepParams p) {
+  chain_wait();
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS, CS>(p.B, p);
   double m = 0.0, j = 0.0;
@@ -176,6 +179,7 @@ __device__ __forceinline__ void os_pull_node(const StepParams &p, Node &nd, cons
 
 template <class C, int AOS, class Node, bool FORCE, bool RED, bool CS>
 __global__ void LBM_STEP_BOUNDS k_os_pull(StepParams p) {
+  chain_wait();
   const auto A = lattice_of<C, AOS>(p.A, p);
   const auto B = lattice_of<C, AOS, CS>(p.B, p);
   double m = 0.0, j = 0.0;
@@ -194,6 +198,7 @@ __global__ void LBM_STEP_BOUNDS k_os_pull(StepParams p) {
 // direction i goes to the node's slot of the opposite direction.
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_aa_even(StepParams p) {
+  chain_wait();
   using T = typename C::T;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
@@ -259,6 +264,7 @@ __device__ __forceinline__ bool aa_fast(const IndirectNode &, const StepParams &
 
 template <class C, int AOS, class Node, bool FORCE, bool RED>
 __global__ void LBM_STEP_BOUNDS k_aa_odd(StepParams p) {
+  chain_wait();
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
   LBM_NODE_LOOP(Node, it) {
@@ -360,6 +366,7 @@ __device__ __forceinline__ void zp_collide_pair(typename PairWord<C>::W (&v)[Q],
 // slots of its own word.
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_even_zp(StepParams p) {
+  chain_wait();
   using W = typename PairWord<C>::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
@@ -422,6 +429,7 @@ __device__ __forceinline__ bool zp_open_plane(const Grid &g, int H, int zw) { re
 // takes the per-node path.
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_odd_zp(StepParams p) {
+  chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
   const Grid &g = p.g;
@@ -475,6 +483,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_o
 // Two-step, kernel 1 in z pairs: A -> B at the same words.
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_collide_zp(StepParams p) {
+  chain_wait();
   using W = typename PairWord<C>::W;
   const Grid &g = p.g;
   const int H = g.nz >> 1;
@@ -501,6 +510,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_c
 // Two-step, kernel 2 in z pairs: A_i(x) = B_i(x - c_i), raw word copies.
 template <class C>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_stream_zp(StepParams p) {
+  chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
   const Grid &g = p.g;
@@ -542,6 +552,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_s
 // One-step push (PUSH) or pull in z pairs.
 template <class C, bool PUSH, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_zp(StepParams p) {
+  chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
   const Grid &g = p.g;
@@ -685,6 +696,7 @@ __device__ __forceinline__ void et_node(const StepParams &p, NodeOf<IND> &nd, co
 
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
+  chain_wait();
   using Node = NodeOf<IND>;
   const auto A = lattice_of<C, AOS>(p.A, p);
   double m = 0.0, j = 0.0;
@@ -706,6 +718,7 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
 // opposite pair exchanged, as in et_node.
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_et_zp(StepParams p) {
+  chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
   const Grid &g = p.g;
@@ -758,16 +771,16 @@ struct LaunchTS {
     if (phase >= 2) {
       if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (phase == 2)
-          k_ts_collide_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_ts_collide_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
         else
-          k_ts_stream_zp<C><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_ts_stream_zp<C>, L.grid, L.block, 0, L.stream, p);
       }
       return;
     }
     if (phase == 0)
-      k_ts_collide<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_ts_collide<C, AOS, NodeOf<IND>, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
     else
-      k_ts_stream<C, AOS, NodeOf<IND>><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_ts_stream<C, AOS, NodeOf<IND>>, L.grid, L.block, 0, L.stream, p);
   }
 };
 // sub: bit 0 = push (else pull), bit 1 = streaming stores (SoA only), bit 2
@@ -777,17 +790,17 @@ struct LaunchOS {
   template <bool CS>
   static void go(const StepParams &p, bool push, const LaunchShape &L) {
     if (push)
-      k_os_push<C, AOS, NodeOf<IND>, FORCE, RED, CS><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_os_push<C, AOS, NodeOf<IND>, FORCE, RED, CS>, L.grid, L.block, 0, L.stream, p);
     else
-      k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED, CS><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_os_pull<C, AOS, NodeOf<IND>, FORCE, RED, CS>, L.grid, L.block, 0, L.stream, p);
   }
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub & 4) {
       if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (sub & 1)
-          k_os_zp<C, true, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_os_zp<C, true, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
         else
-          k_os_zp<C, false, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_os_zp<C, false, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
       }
       return;
     }
@@ -808,16 +821,16 @@ struct LaunchAA {
     if (sub >= 4) {
       if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (sub == 5)
-          k_aa_odd_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_aa_odd_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
         else
-          k_aa_even_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+          launch_chained(k_aa_even_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
       }
       return;
     }
     if (sub)
-      k_aa_odd<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_aa_odd<C, AOS, NodeOf<IND>, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
     else
-      k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+      launch_chained(k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
   }
 };
 // sub: 0 one node per thread, 1 z pairs (FP16 / FP32 storage, SoA, periodic full grid)
@@ -826,10 +839,10 @@ struct LaunchET {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub == 1) {
       if constexpr (kPairable<C> && AOS == 0 && !IND)
-        k_et_zp<C, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+        launch_chained(k_et_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
       return;
     }
-    k_et<C, AOS, IND, FORCE, RED><<<L.grid, L.block, 0, L.stream>>>(p);
+    launch_chained(k_et<C, AOS, IND, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
   }
 };
 

@@ -313,6 +313,7 @@ constexpr int swap_min_blocks() {
 
 template <class C, int AOS, bool FORCE, bool RED, bool FIXED>
 __global__ void __launch_bounds__(256, (swap_min_blocks<C, FIXED>())) k_swap_pass(StepParams p, SwapPass sp) {
+  chain_wait();
   using T = typename C::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = reinterpret_cast<T *>(smem_raw);
@@ -338,6 +339,7 @@ constexpr uint64_t kTmaWaitNs = 1000000000ull;  // 1 s
 
 template <class C, bool FORCE, bool RED, bool FIXED>
 __global__ void __launch_bounds__(256, C::kMinBlocks) k_swap_tma(StepParams p, SwapPass sp, const __grid_constant__ CUtensorMap map) {
+  chain_wait();
   using T = typename C::T;
   using S = typename C::S;
   constexpr bool kInPlace = sizeof(T) == sizeof(S);  // F32, F64: collide into the staged buffer
@@ -418,7 +420,7 @@ struct LaunchSwap {
     const bool fixed = sp.tx == kSwapTX && sp.ty == kSwapTY && sp.tz == kSwapTZ;
     auto k = fixed ? k_swap_pass<C, AOS, FORCE, RED, true> : k_swap_pass<C, AOS, FORCE, RED, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp);
+    launch_chained(k, blocks, dim3(sp.tx, sp.ty, sp.tz), smem, s, p, sp);
   }
 };
 
@@ -441,7 +443,7 @@ struct LaunchSwapTma {
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
       const int grid = std::min(ntiles, per_sm * std::max(nsm, 1));
-      k<<<grid, dim3(sp.tx, sp.ty, sp.tz), smem, s>>>(p, sp, *map);
+      launch_chained(k, dim3(grid), dim3(sp.tx, sp.ty, sp.tz), smem, s, p, sp, *map);
       *launched = grid;
     }
   }
