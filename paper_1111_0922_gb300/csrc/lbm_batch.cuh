@@ -191,9 +191,11 @@ constexpr int batch_min_blocks() {
   return MAXT <= 256 ? C::kMinBlocks : (C::kMinBlocks == 2 ? 1 : 2);
 }
 
-// One step over every active segment: block b takes work chunk b.
+// One step over every active segment: block b takes work chunk b (a chained
+// launch: the next step's blocks may be scheduled while this one drains).
 template <class C, int V, bool RED, int NPT, int MAXT>
 __global__ void __launch_bounds__(MAXT, (batch_min_blocks<C, MAXT>())) k_batch_step(BatchParams p) {
+  chain_wait();
   double m = 0.0, j = 0.0;
   batch_chunk<C, V, NPT>(p, blockIdx.x, p.t, m, j);
   if (RED) block_reduce_store_at(m, j, p.partials, blockIdx.x);
@@ -262,9 +264,9 @@ __global__ void __launch_bounds__(MAXT, (batch_min_blocks<C, MAXT>()))
 template <class C, int V, int NPT, int MAXT>
 static void launch_step_v(bool red, const BatchParams &p, int bs, cudaStream_t s) {
   if (red)
-    k_batch_step<C, V, true, NPT, MAXT><<<p.nwork, bs, 0, s>>>(p);
+    launch_chained(k_batch_step<C, V, true, NPT, MAXT>, dim3(p.nwork), dim3(bs), 0, s, p);
   else
-    k_batch_step<C, V, false, NPT, MAXT><<<p.nwork, bs, 0, s>>>(p);
+    launch_chained(k_batch_step<C, V, false, NPT, MAXT>, dim3(p.nwork), dim3(bs), 0, s, p);
 }
 
 // Persistent round: the grid is every resident block (co-resident, as a
