@@ -416,7 +416,28 @@ struct ZPairCol {
     }
     return w + ex + ey + ez;
   }
+  // INNER: the pair's column is not on an x or y face and its plane is not
+  // next to the seam, so the neighbour word is at the launch-uniform offset
+  // c_i . (1, sx, sxy) and never across the seam
+  template <int SIGN, bool INNER>
+  __device__ __forceinline__ int nbw(const Grid &g, int H, int w, int zw, int i, bool &seam) const {
+    if (INNER) {
+      seam = false;
+      return w + SIGN * (CX(i) + CY(i) * (int)g.sx + CZ(i) * (int)g.sxy);
+    }
+    return nbw<SIGN>(g, H, w, zw, i, seam);
+  }
 };
+
+// Whether every active lane of the warp holds an interior column (no x or
+// y face), decided per warp so that a warp with a face column takes the
+// general path alone instead of running both.
+__device__ __forceinline__ bool zp_inner_warp(const Grid &g, int x, int y) {
+  return __all_sync(__activemask(), x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1);
+}
+__device__ __forceinline__ bool zp_inner_plane(int H, int zw) { return zw > 0 && zw < H - 1; }
+using InnerTag = std::true_type;
+using FaceTag = std::false_type;
 
 // a pair's column and plane have no wall face next to either cell
 __device__ __forceinline__ bool zp_open_column(const Grid &g, int x, int y) {
@@ -440,18 +461,20 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_o
     W *A = static_cast<W *>(p.A);
     const int64_t nw = p.npad >> 1;
     const bool col = zp_open_column(g, x, y);
+    const bool inner = zp_inner_warp(g, x, y);
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
-      if (col && zp_open_plane(g, H, zw)) {
+      auto pair = [&](auto tag) {
+        constexpr bool INNER = decltype(tag)::value;
         const int w = x + (int)g.sx * y + (int)g.sxy * zw;
         W v[Q];
         {
           ZPairCol c;
-          c.set(g, x, y);
+          if (!INNER) c.set(g, x, y);
           v[0] = A[w];
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             bool seam;
-            const W t = A[OPP(i) * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            const W t = A[OPP(i) * nw + c.template nbw<-1, INNER>(g, H, w, zw, i, seam)];
             v[i] = seam ? PW::swap(t) : t;
           }
         }
@@ -459,14 +482,19 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_o
         // recompute the addresses rather than hold them across the collision
         const int ws = launder(w), xs = launder(x), ys = launder(y);
         ZPairCol c;
-        c.set(g, xs, ys);
+        if (!INNER) c.set(g, xs, ys);
         A[ws] = v[0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
           bool seam;
-          const int d = c.nbw<1>(g, H, ws, zw, i, seam);
+          const int d = c.template nbw<1, INNER>(g, H, ws, zw, i, seam);
           A[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
         }
+      };
+      if (inner && zp_inner_plane(H, zw)) {
+        pair(InnerTag{});
+      } else if (col && zp_open_plane(g, H, zw)) {
+        pair(FaceTag{});
       } else {
         const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
         for (int h = 0; h < 2; ++h) {
@@ -521,22 +549,29 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_s
   const W *B = static_cast<const W *>(p.B);
   const int64_t nw = p.npad >> 1;
   const bool col = zp_open_column(g, x, y);
+  const bool inner = zp_inner_warp(g, x, y);
   ZPairCol c;
   c.set(g, x, y);
   for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
-    if (col && zp_open_plane(g, H, zw)) {
+    auto pair = [&](auto tag) {
+      constexpr bool INNER = decltype(tag)::value;
       int w = x + (int)g.sx * y + (int)g.sxy * zw;
       W v[Q];
       v[0] = B[w];
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         bool seam;
-        const W t = B[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+        const W t = B[i * nw + c.template nbw<-1, INNER>(g, H, w, zw, i, seam)];
         v[i] = seam ? PW::swap(t) : t;
       }
       w = launder(w);
 #pragma unroll
       for (int i = 0; i < Q; ++i) A[i * nw + w] = v[i];
+    };
+    if (inner && zp_inner_plane(H, zw)) {
+      pair(InnerTag{});
+    } else if (col && zp_open_plane(g, H, zw)) {
+      pair(FaceTag{});
     } else {
       const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
       ZPairNode a;
@@ -564,8 +599,10 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_z
     W *B = static_cast<W *>(p.B);
     const int64_t nw = p.npad >> 1;
     const bool col = zp_open_column(g, x, y);
+    const bool inner = zp_inner_warp(g, x, y);
     for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
-      if (col && zp_open_plane(g, H, zw)) {
+      auto pair = [&](auto tag) {
+        constexpr bool INNER = decltype(tag)::value;
         const int w = x + (int)g.sx * y + (int)g.sxy * zw;
         W v[Q];
         if (PUSH) {
@@ -573,12 +610,12 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_z
           for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
         } else {
           ZPairCol c;
-          c.set(g, x, y);
+          if (!INNER) c.set(g, x, y);
           v[0] = A[w];
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             bool seam;
-            const W t = A[i * nw + c.nbw<-1>(g, H, w, zw, i, seam)];
+            const W t = A[i * nw + c.template nbw<-1, INNER>(g, H, w, zw, i, seam)];
             v[i] = seam ? PW::swap(t) : t;
           }
         }
@@ -587,18 +624,23 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_z
         const int ws = launder(w), xs = launder(x), ys = launder(y);
         if (PUSH) {
           ZPairCol c;
-          c.set(g, xs, ys);
+          if (!INNER) c.set(g, xs, ys);
           B[ws] = v[0];
 #pragma unroll
           for (int i = 1; i < Q; ++i) {
             bool seam;
-            const int d = c.nbw<1>(g, H, ws, zw, i, seam);
+            const int d = c.template nbw<1, INNER>(g, H, ws, zw, i, seam);
             B[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
           }
         } else {
 #pragma unroll
           for (int i = 0; i < Q; ++i) B[i * nw + ws] = v[i];
         }
+      };
+      if (inner && zp_inner_plane(H, zw)) {
+        pair(InnerTag{});
+      } else if (col && zp_open_plane(g, H, zw)) {
+        pair(FaceTag{});
       } else {
         const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
         for (int h = 0; h < 2; ++h) {
