@@ -305,10 +305,16 @@ __device__ __forceinline__ void swap_tile(const StepParams &p, const SwapPass &s
 
 // One pass: the tiles of one colour, one block per tile.  Full tiles with
 // 4-byte arithmetic fit four blocks per SM (64 registers; measured faster
-// than three, the only spill is a few bytes).
+// than three, the only spill is a few bytes).  Full tiles of FP16 cell
+// pairs fit three (80 registers, no spill; 37.3 against 32.0 GFLUP/s at two
+// on 256^3; four spill several hundred bytes); FP32 pairs stay at two (24.2
+// against 25.5 at three).
 template <class C, bool FIXED>
 constexpr int swap_min_blocks() {
-  return (FIXED && sizeof(typename C::T) == 4) ? 4 : C::kMinBlocks;
+  if constexpr (IsPairCodec<C>::value)
+    return (FIXED && sizeof(typename C::Single::S) == 2) ? 3 : C::kMinBlocks;
+  else
+    return (FIXED && sizeof(typename C::T) == 4) ? 4 : C::kMinBlocks;
 }
 
 template <class C, int AOS, bool FORCE, bool RED, bool FIXED>
