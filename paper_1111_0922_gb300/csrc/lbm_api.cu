@@ -296,13 +296,13 @@ static bool use_ypairs(const lbm_t *h) {
 }
 
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
-// (default 2; 4 for the FP16 AA pattern: 75.1 vs 73.3 GFLUP/s on 256^3,
-// FP32 best at 2)
+// (default 4 with FP16 storage, 2 with FP32; measured on 256^3, FP16 4 vs 2
+// planes: AA 80.3 vs 78.7, one-step push 76.2 vs 74.4 (both kernels
+// prefetch the next plane), pull 79.5 vs 77.5, esoteric twist 80.9 vs 80.2,
+// two-step equal; FP32 best at 2)
 static LaunchShape zpair_shape_of(const lbm_t *h) {
   LaunchShape L = shape_of(h);
-  const int npt = h->cfg.nodes_per_thread > 0
-                      ? h->cfg.nodes_per_thread
-                      : ((h->cfg.variant == LBM_AA && h->cfg.precision == LBM_F16S) ? 4 : 2);
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : (h->cfg.precision == LBM_F16S ? 4 : 2);
   L.grid.z = (unsigned)std::min<int64_t>((h->cfg.nz / 2 + npt - 1) / npt, 65535);
   return L;
 }
