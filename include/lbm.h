@@ -116,10 +116,13 @@ typedef struct lbm_config {
                                 (even nz) in one word per array (4 bytes FP16, 8 bytes FP32), and
                                 one thread updates both; LBM_CG pairs cells y and y + ny/2 instead
                                 (even ny); LBM_SWAP (swap_schedule 0 or 1) pairs z when z is
-                                periodic and nz is a multiple of 4 (at least 8).  0 = default (on
-                                where allowed), 1 = on where allowed, 2 = off (one node per
-                                thread).  The stored layout is internal: lbm_get_pdfs and friends
-                                use natural order. */
+                                periodic and nz is a multiple of 4 (at least 8).  On a node list
+                                (LBM_INDIRECT, SoA, LBM_F16S) LBM_AA pairs consecutive nodes 2t
+                                and 2t + 1 instead (one thread each; the storage order is
+                                unchanged).
+                                0 = default (on where allowed), 1 = on where allowed, 2 = off (one
+                                node per thread).  The stored layout is internal: lbm_get_pdfs and
+                                friends use natural order. */
   void *stream;              /* cudaStream_t the library enqueues on; NULL = default stream */
   lbm_alloc_fn dev_alloc;    /* optional device allocator */
   lbm_free_fn dev_free;      /* required when dev_alloc is given */

@@ -295,6 +295,25 @@ static bool use_ypairs(const lbm_t *h) {
          h->grid.hx == 0 && h->grid.hy == 0;
 }
 
+// AA pattern on a node list in node pairs (k_aa_even_np / k_aa_odd_np in
+// lbm_steps.cuh): FP16 storage, SoA, IDX folded at geometry time, pair_z
+// not 2.
+static bool use_npairs(const lbm_t *h) {
+  const lbm_config &c = h->cfg;
+  return c.variant == LBM_AA && h->idx_folded && c.addressing == LBM_INDIRECT && c.layout == LBM_SOA &&
+         c.precision == LBM_F16S && c.pair_z != 2;
+}
+
+// node pairs: one thread per pair of consecutive nodes, nodes_per_thread
+// pairs per thread (grid-stride; default 2)
+static LaunchShape npair_shape_of(const lbm_t *h) {
+  LaunchShape L = shape_of(h);
+  const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : 2;
+  const int64_t per = (int64_t)L.block.x * npt;
+  L.grid = dim3((unsigned)std::max<int64_t>(1, ((h->nn + 1) / 2 + per - 1) / per));
+  return L;
+}
+
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
 // (default 4 with FP16 storage, 2 with FP32; measured on 256^3, FP16 4 vs 2
 // planes: AA 80.3 vs 78.7, one-step push 76.2 vs 74.4 (both kernels
@@ -815,7 +834,7 @@ lbm_status lbm_get_info(const lbm_t *h, lbm_info *info) {
   info->f16_scale = h->scale;
   info->reduce_blocks = h->partial_blocks;
   info->tile_staged = h->swap_tma ? 1 : 0;
-  info->pair_z = (h->grid.zpair || h->grid.ypair) ? 1 : 0;
+  info->pair_z = (h->grid.zpair || h->grid.ypair || use_npairs(h)) ? 1 : 0;
   return LBM_OK;
 }
 
@@ -1137,6 +1156,10 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
         const LaunchShape L2 = zpair_shape_of(h);
         if (red_blocks) *red_blocks = (int)blocks_of(L2);
         launch_step_kernel(VAR_AA, 4 + (int)(h->steps & 1), p, k, L2);
+      } else if (use_npairs(h)) {
+        const LaunchShape L2 = npair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_AA, 6 + (int)(h->steps & 1), p, k, L2);
       } else {
         launch_step_kernel(VAR_AA, (int)(h->steps & 1), p, k, L);
       }

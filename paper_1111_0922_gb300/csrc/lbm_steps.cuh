@@ -329,6 +329,10 @@ struct PairWord<CodecF16S> {
   __device__ static __forceinline__ W with_lo(W v, float a) { return __halves2half2(CodecF16S::unraw(a), __high2half(v)); }
   __device__ static __forceinline__ W with_hi(W v, float b) { return __halves2half2(__low2half(v), CodecF16S::unraw(b)); }
   __device__ static __forceinline__ W swap(W v) { return __lowhigh2highlow(v); }
+  // raw storage elements of the two cells
+  __device__ static __forceinline__ W pack(__half a, __half b) { return __halves2half2(a, b); }
+  __device__ static __forceinline__ __half lo_s(W v) { return __low2half(v); }
+  __device__ static __forceinline__ __half hi_s(W v) { return __high2half(v); }
 };
 template <>
 struct PairWord<CodecF32> {
@@ -339,6 +343,9 @@ struct PairWord<CodecF32> {
   __device__ static __forceinline__ W with_lo(W v, float a) { return make_float2(a, v.y); }
   __device__ static __forceinline__ W with_hi(W v, float b) { return make_float2(v.x, b); }
   __device__ static __forceinline__ W swap(W v) { return make_float2(v.y, v.x); }
+  __device__ static __forceinline__ W pack(float a, float b) { return make_float2(a, b); }
+  __device__ static __forceinline__ float lo_s(W v) { return v.x; }
+  __device__ static __forceinline__ float hi_s(W v) { return v.y; }
 };
 template <class C>
 constexpr bool kPairable = std::is_same<C, CodecF16S>::value || std::is_same<C, CodecF32>::value;
@@ -519,6 +526,94 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_o
           aa_odd_node<false, C, 0, ZPairNode, FORCE>(p, a, L, m, j);
         }
       }
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+// AA pattern on a node list (SoA, IDX with the bounce-back slots folded in)
+// with FP16 storage, two consecutive nodes per thread: nodes 2t and 2t + 1
+// share word t of every array, so the even step's node-local loads and
+// stores move one 4-byte word for both, and the odd step loads both nodes'
+// IDX entries of a direction as one 8-byte word and gathers the two PDFs
+// into one register word.  The per-node arithmetic is that of the
+// one-node-per-thread kernels (bit-identical results); the last node of an
+// odd count takes the per-node path.  64 registers (four 256-thread blocks
+// per SM; the odd kernel spills a few dozen bytes with a force), two pairs
+// per thread by default: 512^3 sphere pack 50.4 against 45.4 GFLUP/s one
+// node per thread (three blocks: 47.5; two: 43.2).  FP32 pairs (30.5-33.3
+// against 34.7) and esoteric-twist pairs (FP16 36.3-41.2 against 43.0)
+// measured slower and are not built.
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, 4) k_aa_even_np(StepParams p) {
+  chain_wait();
+  using W = typename PairWord<C>::W;
+  const int64_t nn = p.nnodes, nt = (nn + 1) >> 1;
+  W *A = static_cast<W *>(p.A);
+  const int64_t nw = p.npad >> 1;
+  double m = 0.0, j = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    if (2 * t + 1 < nn) {
+      int w = (int)t;
+      W v[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
+      zp_collide_pair<C, FORCE>(v, p, m, j);
+      w = launder(w);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) A[OPP(i) * nw + w] = v[i];
+    } else {
+      const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
+      typename C::T d[Q];
+      const int s = (int)(2 * t);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = L.ld(i, s);
+      run_collision<C, FORCE>(d, p, m, j);
+      const int s2 = launder(s);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) L.st(OPP(i), s2, d[i]);
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, 4) k_aa_odd_np(StepParams p) {
+  chain_wait();
+  using PW = PairWord<C>;
+  using W = typename PW::W;
+  using S = typename C::S;
+  const int64_t nn = p.nnodes, nt = (nn + 1) >> 1;
+  S *E = static_cast<S *>(p.A);
+  W *A = static_cast<W *>(p.A);
+  const int64_t nw = p.npad >> 1;
+  const int2 *I = reinterpret_cast<const int2 *>(p.idx);
+  const int64_t iw = p.ipad >> 1;  // IDX words (two nodes) per direction
+  double m = 0.0, j = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    if (2 * t + 1 < nn) {
+      const int w = (int)t;
+      W v[Q];
+      v[0] = A[w];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int2 src = __ldg(I + (OPP(i) - 1) * iw + w);  // x - c_i of both nodes
+        v[i] = PW::pack(E[OPP(i) * p.npad + src.x], E[OPP(i) * p.npad + src.y]);
+      }
+      zp_collide_pair<C, FORCE>(v, p, m, j);
+      const int ws = launder(w);
+      A[ws] = v[0];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int2 dst = __ldg(I + (i - 1) * iw + ws);  // x + c_i
+        E[i * p.npad + dst.x] = PW::lo_s(v[i]);
+        E[i * p.npad + dst.y] = PW::hi_s(v[i]);
+      }
+    } else {
+      const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
+      IndirectNode nd;
+      nd.init(p, 2 * t);
+      aa_odd_node<true, C, 0, IndirectNode, FORCE>(p, nd, L, m, j);
     }
   }
   if (RED) block_reduce_store(m, j, p.partials);
@@ -918,11 +1013,18 @@ struct LaunchOS {
   }
 };
 // sub: 0 even, 1 odd (one node per thread); 4 even, 5 odd (z pairs, FP16 /
-// FP32 storage, SoA full grid)
+// FP32 storage, SoA full grid); 6 even, 7 odd (node pairs, FP16 storage,
+// SoA node list with folded IDX)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchAA {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub >= 4) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && IND) {
+        if (sub == 7)
+          launch_chained(k_aa_odd_np<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
+        else if (sub == 6)
+          launch_chained(k_aa_even_np<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
+      }
       if constexpr (kPairable<C> && AOS == 0 && !IND) {
         if (sub == 5)
           launch_chained(k_aa_odd_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);

@@ -213,9 +213,78 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     assert lat.info.pair_z == 0
     lat.close()
     for variant, kw in (("aa", {"precision": "f64"}), ("os_push", {"store_hint": 1}),
-                        ("aa", {"layout": "aos"}), ("aa", {"addressing": "indirect"}), ("aa", {"pair_z": 2})):
+                        ("aa", {"layout": "aos"}), ("os_pull", {"addressing": "indirect"}), ("aa", {"pair_z": 2}),
+                        ("aa", {"addressing": "indirect", "pair_z": 2}), ("et", {"addressing": "indirect"}),
+                        ("aa", {"addressing": "indirect", "precision": "f32"}),
+                        ("aa", {"addressing": "indirect", "precision": "f64"})):
         kw.setdefault("precision", "f16s")
         lat = L.Lattice((16, 8, 6), (1, 1, 1), variant=variant, **kw)
         lat.set_geometry(None)
         assert lat.info.pair_z == 0, variant
         lat.close()
+
+
+NODE_CASES = [
+    ((16, 8, 6), (1, 1, 1), 0.15),
+    ((17, 9, 7), (1, 0, 1), 0.2),
+    ((24, 10, 12), (0, 0, 0), 0.1),
+    ((33, 7, 10), (1, 1, 0), 0.3),
+    ((5, 3, 3), (1, 1, 1), 0.0),
+]
+
+
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("dims,per,solid_frac", NODE_CASES)
+def test_node_pairs_equal_single_nodes_bitwise(L, dims, per, solid_frac, force):
+    """AA pattern on a node list with FP16 storage: consecutive nodes 2t and
+    2t + 1 in one thread (one word per array for the even step, one 8-byte
+    IDX word and two gathers per direction for the odd step) against one
+    node per thread, with odd and even node counts (the last node of an odd
+    count alone), solid links folded into the IDX, walls and periodic axes,
+    several pairs per thread."""
+    variant, precision = "aa", "f16s"
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(n + 7 * force)
+    solid = (rng.random(n) < solid_frac).astype(np.uint8)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, -1e-5, 5e-6) if force else (0.0, 0.0, 0.0)
+    fl = solid == 0
+    for steps in (2, 4, 6):
+        out = []
+        for pz in (0, 2):
+            lat = L.Lattice(dims, per, variant=variant, addressing="indirect", precision=precision, omega=1.3,
+                            force=g, pair_z=pz)
+            lat.set_geometry(solid)
+            cells = lat.nodes()
+            assert np.array_equal(cells, np.flatnonzero(fl))
+            lat.set_pdfs(f0[:, cells])  # node order
+            lat.step(steps)
+            m, j = lat.step_flux(2)  # sums of the state after `steps`, fused into the next step
+            out.append((lat.pdfs(), lat.info.pair_z, int(lat.info.nodes), m, j))
+            lat.close()
+        (a, pa, na, ma, ja), (b, pb, nb, mb, jb) = out
+        assert pa == 1 and pb == 0 and na == nb == int(fl.sum())
+        assert np.array_equal(a, b), (dims, per, steps)
+        assert abs(ma - mb) <= 1e-12 * abs(mb) and abs(ja - jb) <= 1e-12 * max(abs(jb), 1e-30)
+
+
+def test_node_pairs_match_oracle(L):
+    variant, precision = "aa", "f16s"
+    dims, per = (24, 10, 12), (1, 1, 0)
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(11)
+    solid = (rng.random(n) < 0.2).astype(np.uint8)
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (1e-5, 0.0, -2e-5)
+    lat = L.Lattice(dims, per, variant=variant, addressing="indirect", precision=precision, omega=1.3, force=g)
+    lat.set_geometry(solid)
+    cells = lat.nodes()
+    lat.set_pdfs(f0[:, cells])
+    lat.step(8)
+    out = lat.pdfs()
+    assert lat.info.pair_z == 1
+    lat.close()
+    ref = oracle.run_push(dims, per, solid, f0, 8, 1.3, g)
+    _, ug = oracle.macroscopics(out, g)
+    _, uo = oracle.macroscopics(ref[:, cells], g)
+    assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= TOL_U[precision]
