@@ -263,7 +263,9 @@ lbm_status lbm_solve_permeability(lbm_t *h, int32_t check, double tol, int64_t m
  * persistent cooperative launch for all k steps (round_mode).  Its first
  * step also reduces each geometry's mass and flux (FP64, per 4096-aligned
  * chunk, then summed in chunk order), so a geometry's results are
- * bit-identical alone and in any mix, in either round mode.  After each
+ * bit-identical alone and in any mix, in either round mode (its PDFs with
+ * any launch shape, its sums with the same block size and nodes per
+ * thread; other shapes differ in the last bits).  After each
  * round the library applies each geometry's steady-flux test (relative flux
  * change between consecutive rounds below its tol) and computes its
  * permeability.  Admissions build their geometry on a second stream, so

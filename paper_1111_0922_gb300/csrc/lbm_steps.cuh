@@ -314,42 +314,6 @@ struct ZPairNode {
   }
 };
 
-// Word of a cell pair: both cells' storage in one aligned word (FP16: the
-// lower cell in the low half; FP32: in .x).  kMinBlocks: resident 256-thread
-// blocks per SM of the pair kernels (FP32 pairs hold both cells' 38 values,
-// so they get 128 registers; measured faster than 80 with spills).
-template <class C>
-struct PairWord;
-template <>
-struct PairWord<CodecF16S> {
-  using W = __half2;
-  static constexpr int kMinBlocks = 3;
-  __device__ static __forceinline__ float lo(W v) { return CodecF16S::raw(__low2half(v)); }
-  __device__ static __forceinline__ float hi(W v) { return CodecF16S::raw(__high2half(v)); }
-  __device__ static __forceinline__ W with_lo(W v, float a) { return __halves2half2(CodecF16S::unraw(a), __high2half(v)); }
-  __device__ static __forceinline__ W with_hi(W v, float b) { return __halves2half2(__low2half(v), CodecF16S::unraw(b)); }
-  __device__ static __forceinline__ W swap(W v) { return __lowhigh2highlow(v); }
-  // raw storage elements of the two cells
-  __device__ static __forceinline__ W pack(__half a, __half b) { return __halves2half2(a, b); }
-  __device__ static __forceinline__ __half lo_s(W v) { return __low2half(v); }
-  __device__ static __forceinline__ __half hi_s(W v) { return __high2half(v); }
-};
-template <>
-struct PairWord<CodecF32> {
-  using W = float2;
-  static constexpr int kMinBlocks = 2;
-  __device__ static __forceinline__ float lo(W v) { return v.x; }
-  __device__ static __forceinline__ float hi(W v) { return v.y; }
-  __device__ static __forceinline__ W with_lo(W v, float a) { return make_float2(a, v.y); }
-  __device__ static __forceinline__ W with_hi(W v, float b) { return make_float2(v.x, b); }
-  __device__ static __forceinline__ W swap(W v) { return make_float2(v.y, v.x); }
-  __device__ static __forceinline__ W pack(float a, float b) { return make_float2(a, b); }
-  __device__ static __forceinline__ float lo_s(W v) { return v.x; }
-  __device__ static __forceinline__ float hi_s(W v) { return v.y; }
-};
-template <class C>
-constexpr bool kPairable = std::is_same<C, CodecF16S>::value || std::is_same<C, CodecF32>::value;
-
 // Collide both cells of a pair word by word: v[i] holds f_i of the lower and
 // of the upper cell, raw storage units.
 template <class C, bool FORCE>

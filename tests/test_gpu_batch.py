@@ -63,22 +63,37 @@ def test_batch_matches_oracle(L, variant, precision, mode):
     b.close()
 
 
+@pytest.mark.parametrize("mix_npt", [2, 4])
 @pytest.mark.parametrize("mix_mode", [0, 1])
 @pytest.mark.parametrize("variant", ["aa", "et"])
-def test_alone_equals_mix_bitwise(L, variant, mix_mode):
-    """One geometry alone (per-step launches, 256 x 1) and in a mix with
-    other geometries admitted earlier and later (another launch shape, either
-    round mode): the same bits."""
+@pytest.mark.parametrize("precision", ["f32", "f16s"])
+def test_alone_equals_mix_bitwise(L, precision, variant, mix_mode, mix_npt):
+    """One geometry alone and in a mix with other geometries admitted
+    earlier and later, with the same launch shape (either round mode): the
+    same PDF and flux bits.  Against a third run with another shape (256 x 1,
+    per-step launches; with FP16 storage the AA pattern's mix runs node pairs
+    and this one one node per thread): the same PDF bits, and flux sums that
+    differ at most in the last bits (the threads group the nodes' FP64
+    terms differently)."""
     packs = _packs()
     target = packs[0]
-    alone = L.Batch(16384, variant=variant, precision="f32", max_geometries=4)
-    s_alone = alone.admit(*target)
-    fl_alone = []
-    for _ in range(3):
-        alone.round(4)
-        fl_alone.append(alone.flux(s_alone))
-    mix = L.Batch(4 * 16384, variant=variant, precision="f32", max_geometries=8, block_size=512 if mix_mode else 128,
-                  nodes_per_thread=2, round_mode=mix_mode)
+    kw = {"f16_scale": 2.0 ** 20} if precision == "f16s" else {}
+    shape = dict(block_size=512 if mix_mode else 128, nodes_per_thread=mix_npt, round_mode=mix_mode)
+
+    def run_alone(**sh):
+        b = L.Batch(16384, variant=variant, precision=precision, max_geometries=4, **sh, **kw)
+        s = b.admit(*target)
+        fl = []
+        for _ in range(3):
+            b.round(4)
+            fl.append(b.flux(s))
+        out = b.pdfs(s)
+        b.close()
+        return fl, out
+
+    fl_alone, a = run_alone(**shape)
+    fl_ref, r = run_alone(block_size=256, nodes_per_thread=1)
+    mix = L.Batch(4 * 16384, variant=variant, precision=precision, max_geometries=8, **shape, **kw)
     other = mix.admit(*packs[1])
     mix.round(3)  # the other geometry is at an odd step count when the target arrives
     s_mix = mix.admit(*target)
@@ -88,12 +103,12 @@ def test_alone_equals_mix_bitwise(L, variant, mix_mode):
         mix.round(4)
         fl_mix.append(mix.flux(s_mix))
     assert mix.flux(other)[2] == 15
-    assert fl_mix == fl_alone
-    a = alone.pdfs(s_alone)
     m = mix.pdfs(s_mix)
-    assert np.array_equal(a, m)
-    alone.close()
     mix.close()
+    assert fl_mix == fl_alone
+    assert np.array_equal(a, m) and np.array_equal(r, m)
+    for (ma, ja, sa), (mb, jb, sb) in zip(fl_mix, fl_ref):
+        assert sa == sb and abs(ma - mb) <= 1e-12 * mb and abs(ja - jb) <= 1e-12 * max(abs(jb), 1e-30)
 
 
 def test_release_reuse_and_capacity(L):
@@ -228,15 +243,16 @@ def test_step_cap_and_release_from_poll(L):
     b.close()
 
 
+@pytest.mark.parametrize("npt", [1, 2, 8])
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
-def test_folded_and_plain_idx_agree(L, precision):
+def test_folded_and_plain_idx_agree(L, precision, npt):
     """The AA pattern's batch IDX with bounce-back slots folded in (the
     default below 2^30 slots) and with -1 kept for solid links give the same
-    bits."""
+    bits (FP16 with two or eight nodes per thread: node pairs)."""
     outs = []
     for keep in (0, 1):
         b = L.Batch(3 * 16384, variant="aa", precision=precision, max_geometries=8, keep_idx=keep,
-                    f16_scale=2.0 ** 20 if precision == "f16s" else 0.0)
+                    block_size=128, nodes_per_thread=npt, f16_scale=2.0 ** 20 if precision == "f16s" else 0.0)
         slots = [b.admit(p, om, g) for p, om, g in _packs()]
         b.round(5)
         b.round(3)
