@@ -117,9 +117,9 @@ typedef struct lbm_config {
                                 one thread updates both; LBM_CG pairs cells y and y + ny/2 instead
                                 (even ny); LBM_SWAP (swap_schedule 0 or 1) pairs z when z is
                                 periodic and nz is a multiple of 4 (at least 8).  On a node list
-                                (LBM_INDIRECT, SoA, LBM_F16S) LBM_AA pairs consecutive nodes 2t
-                                and 2t + 1 instead (one thread each; the storage order is
-                                unchanged).
+                                (LBM_INDIRECT, SoA, LBM_F16S) LBM_AA and LBM_ET pair consecutive
+                                nodes 2t and 2t + 1 instead (one thread each; the storage order
+                                is unchanged).
                                 0 = default (on where allowed), 1 = on where allowed, 2 = off (one
                                 node per thread).  The stored layout is internal: lbm_get_pdfs and
                                 friends use natural order. */

@@ -295,13 +295,13 @@ static bool use_ypairs(const lbm_t *h) {
          h->grid.hx == 0 && h->grid.hy == 0;
 }
 
-// AA pattern on a node list in node pairs (k_aa_even_np / k_aa_odd_np in
-// lbm_steps.cuh): FP16 storage, SoA, IDX folded at geometry time, pair_z
-// not 2.
+// AA pattern (IDX folded at geometry time) and esoteric twist on a node list
+// in node pairs (k_aa_even_np / k_aa_odd_np / k_et_np in lbm_steps.cuh):
+// FP16 storage, SoA, pair_z not 2.
 static bool use_npairs(const lbm_t *h) {
   const lbm_config &c = h->cfg;
-  return c.variant == LBM_AA && h->idx_folded && c.addressing == LBM_INDIRECT && c.layout == LBM_SOA &&
-         c.precision == LBM_F16S && c.pair_z != 2;
+  return ((c.variant == LBM_AA && h->idx_folded) || c.variant == LBM_ET) && c.addressing == LBM_INDIRECT &&
+         c.layout == LBM_SOA && c.precision == LBM_F16S && c.pair_z != 2;
 }
 
 // node pairs: one thread per pair of consecutive nodes, nodes_per_thread
@@ -1171,6 +1171,10 @@ static lbm_status one_step(lbm_t *h, bool red, int *red_blocks = nullptr) {
         const LaunchShape L2 = zpair_shape_of(h);
         if (red_blocks) *red_blocks = (int)blocks_of(L2);
         launch_step_kernel(VAR_ET, 1, p, k, L2);
+      } else if (use_npairs(h)) {
+        const LaunchShape L2 = npair_shape_of(h);
+        if (red_blocks) *red_blocks = (int)blocks_of(L2);
+        launch_step_kernel(VAR_ET, 2, p, k, L2);
       } else {
         launch_step_kernel(VAR_ET, 0, p, k, L);
       }

@@ -506,8 +506,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_o
 // per SM; the odd kernel spills a few dozen bytes with a force), two pairs
 // per thread by default: 512^3 sphere pack 50.4 against 45.4 GFLUP/s one
 // node per thread (three blocks: 47.5; two: 43.2).  FP32 pairs (30.5-33.3
-// against 34.7) and esoteric-twist pairs (FP16 36.3-41.2 against 43.0)
-// measured slower and are not built.
+// against 34.7) measured slower and are not built.
 template <class C, bool FORCE, bool RED>
 __global__ void __launch_bounds__(LBM_STEP_MAXT, 4) k_aa_even_np(StepParams p) {
   chain_wait();
@@ -924,6 +923,70 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_et_z
   if (RED) block_reduce_store(m, j, p.partials);
 }
 
+// Esoteric twist on an FP16 node list (SoA) in node pairs: nodes 2t and
+// 2t + 1 share word t of every array, so the own-slot loads and stores
+// (rest and odd directions in, even directions out) move one word for both
+// nodes, and the packed index words of both come as one 8-byte word per
+// direction; the neighbour positions are gathered and scattered per node.
+// The index words are loaded again for the stores (L1 hits) instead of
+// being held across the collision.  Where the two nodes send an even
+// direction to different arrays (one of them has a solid link) the two
+// halves are stored apart.  The per-node arithmetic is et_node's
+// (bit-identical results).  80 registers (three blocks per SM), two pairs
+// per thread: 512^3 sphere pack 44.0 against 42.6 GFLUP/s one node per
+// thread (four blocks 42.3; the index words held in registers 41.2).
+template <class C, bool FORCE, bool RED>
+__global__ void __launch_bounds__(LBM_STEP_MAXT, 3) k_et_np(StepParams p) {
+  chain_wait();
+  using PW = PairWord<C>;
+  using W = typename PW::W;
+  using S = typename C::S;
+  const int64_t nn = p.nnodes, nt = (nn + 1) >> 1;
+  auto arr = [&](int k) { return static_cast<W *>(p.mapbase[k]); };
+  auto el = [&](int k) { return static_cast<S *>(p.mapbase[k]); };
+  const uint2 *I = reinterpret_cast<const uint2 *>(p.idx);
+  const int64_t iw = p.ipad >> 1;
+  double m = 0.0, j = 0.0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    if (2 * t + 1 < nn) {
+      const int w = (int)t;
+      W v[Q];
+      v[0] = arr(0)[w];
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        const int i = 2 * k - 1;
+        const uint2 q = __ldg(I + (k - 1) * iw + w);
+        v[i] = arr(i)[w];
+        v[i + 1] = PW::pack(el(i + 1)[q.x & 0x7fffffffu], el(i + 1)[q.y & 0x7fffffffu]);
+      }
+      zp_collide_pair<C, FORCE>(v, p, m, j);
+      const int ws = launder(w);
+      arr(0)[ws] = v[0];
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        const int i = 2 * k - 1;
+        const uint2 q = __ldg(I + (k - 1) * iw + ws);
+        const int pa = (int)(q.x & 0x7fffffffu), pb = (int)(q.y & 0x7fffffffu);
+        el(pa < p.nfluid ? i + 1 : i)[pa] = PW::lo_s(v[i]);
+        el(pb < p.nfluid ? i + 1 : i)[pb] = PW::hi_s(v[i]);
+        const bool la = (q.x >> 31) == 0u, lb = (q.y >> 31) == 0u;
+        if (la == lb) {
+          arr(la ? i : i + 1)[ws] = v[i + 1];
+        } else {
+          el(la ? i : i + 1)[2 * ws] = PW::lo_s(v[i + 1]);
+          el(lb ? i : i + 1)[2 * ws + 1] = PW::hi_s(v[i + 1]);
+        }
+      }
+    } else {
+      const Lattice<C, 0> L = lattice_of<C, 0>(p.A, p);
+      IndirectNode nd;
+      nd.init(p, 2 * t);
+      et_node<false, C, 0, true, FORCE>(p, nd, L, m, j);
+    }
+  }
+  if (RED) block_reduce_store(m, j, p.partials);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 
@@ -1003,13 +1066,19 @@ struct LaunchAA {
       launch_chained(k_aa_even<C, AOS, NodeOf<IND>, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
   }
 };
-// sub: 0 one node per thread, 1 z pairs (FP16 / FP32 storage, SoA, periodic full grid)
+// sub: 0 one node per thread, 1 z pairs (FP16 / FP32 storage, SoA, periodic
+// full grid), 2 node pairs (FP16 storage, SoA node list)
 template <class C, int AOS, bool IND, bool FORCE, bool RED>
 struct LaunchET {
   static void run(const StepParams &p, int sub, const LaunchShape &L) {
     if (sub == 1) {
       if constexpr (kPairable<C> && AOS == 0 && !IND)
         launch_chained(k_et_zp<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
+      return;
+    }
+    if (sub == 2) {
+      if constexpr (std::is_same<C, CodecF16S>::value && AOS == 0 && IND)
+        launch_chained(k_et_np<C, FORCE, RED>, L.grid, L.block, 0, L.stream, p);
       return;
     }
     launch_chained(k_et<C, AOS, IND, FORCE, RED>, L.grid, L.block, 0, L.stream, p);

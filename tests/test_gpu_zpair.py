@@ -214,7 +214,8 @@ def test_pairs_off_with_solids_or_odd_nz(L):
     lat.close()
     for variant, kw in (("aa", {"precision": "f64"}), ("os_push", {"store_hint": 1}),
                         ("aa", {"layout": "aos"}), ("os_pull", {"addressing": "indirect"}), ("aa", {"pair_z": 2}),
-                        ("aa", {"addressing": "indirect", "pair_z": 2}), ("et", {"addressing": "indirect"}),
+                        ("aa", {"addressing": "indirect", "pair_z": 2}), ("et", {"addressing": "indirect", "pair_z": 2}),
+                        ("et", {"addressing": "indirect", "precision": "f32"}),
                         ("aa", {"addressing": "indirect", "precision": "f32"}),
                         ("aa", {"addressing": "indirect", "precision": "f64"})):
         kw.setdefault("precision", "f16s")
@@ -235,14 +236,16 @@ NODE_CASES = [
 
 @pytest.mark.parametrize("force", [False, True])
 @pytest.mark.parametrize("dims,per,solid_frac", NODE_CASES)
-def test_node_pairs_equal_single_nodes_bitwise(L, dims, per, solid_frac, force):
-    """AA pattern on a node list with FP16 storage: consecutive nodes 2t and
-    2t + 1 in one thread (one word per array for the even step, one 8-byte
-    IDX word and two gathers per direction for the odd step) against one
-    node per thread, with odd and even node counts (the last node of an odd
-    count alone), solid links folded into the IDX, walls and periodic axes,
-    several pairs per thread."""
-    variant, precision = "aa", "f16s"
+@pytest.mark.parametrize("variant", ["aa", "et"])
+def test_node_pairs_equal_single_nodes_bitwise(L, variant, dims, per, solid_frac, force):
+    """AA pattern and esoteric twist on a node list with FP16 storage:
+    consecutive nodes 2t and 2t + 1 in one thread (one word per array for
+    the own-slot loads and stores, one 8-byte index word and two gathers per
+    direction for the neighbour slots) against one node per thread, with odd
+    and even node counts (the last node of an odd count alone), solid links
+    (folded into the AA pattern's IDX; ghost slots and split stores in the
+    esoteric twist), walls and periodic axes, several pairs per thread."""
+    precision = "f16s"
     n = int(np.prod(dims))
     rng = np.random.default_rng(n + 7 * force)
     solid = (rng.random(n) < solid_frac).astype(np.uint8)
@@ -268,8 +271,9 @@ def test_node_pairs_equal_single_nodes_bitwise(L, dims, per, solid_frac, force):
         assert abs(ma - mb) <= 1e-12 * abs(mb) and abs(ja - jb) <= 1e-12 * max(abs(jb), 1e-30)
 
 
-def test_node_pairs_match_oracle(L):
-    variant, precision = "aa", "f16s"
+@pytest.mark.parametrize("variant", ["aa", "et"])
+def test_node_pairs_match_oracle(L, variant):
+    precision = "f16s"
     dims, per = (24, 10, 12), (1, 1, 0)
     n = int(np.prod(dims))
     rng = np.random.default_rng(11)
