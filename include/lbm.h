@@ -97,8 +97,10 @@ typedef struct lbm_config {
                                 half-way for Poiseuille flow) */
   int32_t block_size;        /* threads per block of the step kernels (multiple of 32, <= 256); 0 = 128
                                 (256 for LBM_AA on a node list) */
-  int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default (full grid: 2 planes;
-                                node list: 1 node) */
+  int32_t nodes_per_thread;  /* nodes each thread updates (1..16); 0 = default (full grid: 2 planes,
+                                4 pair planes with FP16 cell pairs; node list: 1 node, 2 node
+                                pairs with FP16 node pairs); with cell or node pairs it counts
+                                pairs */
   int32_t cg_shift;          /* LBM_CG: full grid: shift k >= 2 planes (slabs of k-1 planes, k extra
                                 planes of storage; 0 = slabs of about 2^22 cells);
                                 node list: slab size B >= 1 nodes (0 = 2^21) */
@@ -274,7 +276,9 @@ typedef struct lbm_batch_config {
   int32_t variant;           /* LBM_AA or LBM_ET (the starting variant when tune_variant = 1) */
   int32_t precision;         /* LBM_F64, LBM_F32, LBM_F16S */
   int32_t block_size;        /* threads per block: 64, 128, 256 or 512; 0 = 256 */
-  int32_t nodes_per_thread;  /* 1, 2, 4 or 8; block_size * nodes_per_thread divides 4096; 0 = 1 */
+  int32_t nodes_per_thread;  /* 1, 2, 4 or 8; block_size * nodes_per_thread divides 4096; 0 = 1;
+                                with LBM_F16S and LBM_AA, 2 or more run the chunk's nodes in
+                                consecutive pairs (nodes_per_thread / 2 pairs per thread) */
   int64_t capacity_slots;    /* node slots of the shared arrays (rounded up to 4096) */
   int32_t max_geometries;    /* size of the geometry table */
   int32_t keep_idx;          /* LBM_AA: 1 = IDX keeps -1 for solid links; 0 = bounce-back slots

@@ -292,3 +292,36 @@ def test_node_pairs_match_oracle(L, variant):
     _, ug = oracle.macroscopics(out, g)
     _, uo = oracle.macroscopics(ref[:, cells], g)
     assert np.max(np.abs(ug - uo)) / np.max(np.abs(uo)) <= TOL_U[precision]
+
+
+@pytest.mark.parametrize("variant", ["aa", "et"])
+@pytest.mark.parametrize("nfluid", [1, 2, 3, 64, 65])
+def test_node_pairs_tiny_lists(L, variant, nfluid):
+    """Node lists of one, two and three nodes (a lone last node, one pair, a
+    pair and a lone node) and of 64 / 65 nodes, with FP16 node pairs against
+    one node per thread; every other cell solid."""
+    dims, per = (5, 4, 4), (1, 1, 1)
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(nfluid)
+    solid = np.ones(n, np.uint8)
+    solid[np.sort(rng.choice(n, nfluid, replace=False))] = 0
+    f0 = oracle.rest_state(n) * (1 + 0.02 * (rng.random((19, n)) - 0.5))
+    g = (2e-5, 0.0, 1e-5)
+    out = []
+    for pz in (0, 2):
+        lat = L.Lattice(dims, per, variant=variant, addressing="indirect", precision="f16s", omega=1.2, force=g,
+                        pair_z=pz)
+        lat.set_geometry(solid)
+        cells = lat.nodes()
+        assert cells.size == nfluid
+        lat.set_pdfs(f0[:, cells])
+        lat.step(4)
+        out.append((lat.pdfs(), lat.info.pair_z))
+        lat.close()
+    (a, pa), (b, pb) = out
+    assert pa == 1 and pb == 0
+    assert np.array_equal(a, b)
+    ref = oracle.run_push(dims, per, solid, f0, 4, 1.2, g)
+    _, ug = oracle.macroscopics(a, g)
+    _, uo = oracle.macroscopics(ref[:, cells], g)
+    assert np.max(np.abs(ug - uo)) <= 2e-3 * max(np.max(np.abs(uo)), 1e-12) + 1e-9
