@@ -314,6 +314,16 @@ struct ZPairNode {
   }
 };
 
+// Resident 256-thread blocks per SM of the FP16 pair kernels whose loads are
+// neighbour words (AA odd step, one-step pull): four (64 registers; 256^3:
+// AA 82.1 against 80.0 GFLUP/s, pull 84.3 against 79.2); the others keep
+// PairWord's three (four measured slower: AA even step 78.6, push 60.1,
+// esoteric twist 69.8).
+template <class C, bool NEIGHBOUR_LOADS>
+constexpr int pair_read_min_blocks() {
+  return (std::is_same<C, CodecF16S>::value && NEIGHBOUR_LOADS) ? 4 : PairWord<C>::kMinBlocks;
+}
+
 // Collide both cells of a pair word by word: v[i] holds f_i of the lower and
 // of the upper cell, raw storage units.
 template <class C, bool FORCE>
@@ -340,7 +350,7 @@ __device__ __forceinline__ void zp_collide_pair(typename PairWord<C>::W (&v)[Q],
 // arithmetic (FP16 78.1 -> 80.3 GFLUP/s on 256^3 with four planes per
 // thread; FP32 unchanged).
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_even_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (PairWord<C>::kMinBlocks)) k_aa_even_zp(StepParams p) {
   chain_wait();
   using W = typename PairWord<C>::W;
   const Grid &g = p.g;
@@ -436,7 +446,7 @@ __device__ __forceinline__ bool zp_open_plane(const Grid &g, int H, int zw) { re
 // in, the words at x + c_i out.  A pair with a wall face next to either cell
 // takes the per-node path.
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_aa_odd_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_read_min_blocks<C, true>())) k_aa_odd_zp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
@@ -664,7 +674,7 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_s
 // planes per thread).  The pull and the AA odd step read neighbour words;
 // the same prefetch there measured 3 % slower (AA odd, FP16).
 template <class C, bool PUSH, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_os_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_read_min_blocks<C, !PUSH>())) k_os_zp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
@@ -879,7 +889,7 @@ __global__ void LBM_ET_BOUNDS k_et(StepParams p) {
 // post-collision PDFs go back to the same words with the arrays of each
 // opposite pair exchanged, as in et_node.
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_et_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (PairWord<C>::kMinBlocks)) k_et_zp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
