@@ -129,8 +129,12 @@ struct YPairNode {
   }
 };
 
+// FP16 y pairs at four resident blocks per SM (64 registers; the loads are
+// neighbour words, as in the AA odd step: 256^3 73.7 against 68.8 GFLUP/s
+// at three); FP32 pairs at PairWord's two.
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(256, PairWord<C>::kMinBlocks) k_cg_slab_yp(StepParams p) {
+__global__ void __launch_bounds__(256, (std::is_same<C, CodecF16S>::value ? 4 : PairWord<C>::kMinBlocks))
+    k_cg_slab_yp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
