@@ -316,9 +316,9 @@ static LaunchShape npair_shape_of(const lbm_t *h) {
 
 // one thread per column (x, y) and pair plane, nodes_per_thread pair planes
 // (default 4 with FP16 storage, 2 with FP32; measured on 256^3, FP16 4 vs 2
-// planes: AA 80.3 vs 78.7, one-step push 76.2 vs 74.4 (both kernels
-// prefetch the next plane), pull 79.5 vs 77.5, esoteric twist 80.9 vs 80.2,
-// two-step equal; FP32 best at 2)
+// planes: AA 80.3 vs 78.7 (its even kernel prefetches the next plane),
+// one-step push 77.9 vs 76.2, pull 79.5 vs 77.5, esoteric twist 80.9 vs
+// 80.2, two-step equal; FP32 best at 2)
 static LaunchShape zpair_shape_of(const lbm_t *h) {
   LaunchShape L = shape_of(h);
   const int npt = h->cfg.nodes_per_thread > 0 ? h->cfg.nodes_per_thread : (h->cfg.precision == LBM_F16S ? 4 : 2);

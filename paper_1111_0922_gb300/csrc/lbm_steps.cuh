@@ -314,14 +314,14 @@ struct ZPairNode {
   }
 };
 
-// Resident 256-thread blocks per SM of the FP16 pair kernels whose loads are
-// neighbour words (AA odd step, one-step pull): four (64 registers; 256^3:
-// AA 82.1 against 80.0 GFLUP/s, pull 84.3 against 79.2); the others keep
-// PairWord's three (four measured slower: AA even step 78.6, push 60.1,
-// esoteric twist 69.8).
-template <class C, bool NEIGHBOUR_LOADS>
-constexpr int pair_read_min_blocks() {
-  return (std::is_same<C, CodecF16S>::value && NEIGHBOUR_LOADS) ? 4 : PairWord<C>::kMinBlocks;
+// Resident 256-thread blocks per SM of the FP16 AA odd-step and one-step
+// pair kernels: four (64 registers; 256^3: AA 82.1 against 80.0 GFLUP/s,
+// pull 84.3 against 79.2, push 77.9 against 76.2 with the next plane
+// prefetched at three); the others keep PairWord's three (four measured
+// slower: AA even step 78.6, esoteric twist 69.8).
+template <class C>
+constexpr int pair_four_min_blocks() {
+  return std::is_same<C, CodecF16S>::value ? 4 : PairWord<C>::kMinBlocks;
 }
 
 // Collide both cells of a pair word by word: v[i] holds f_i of the lower and
@@ -446,7 +446,7 @@ __device__ __forceinline__ bool zp_open_plane(const Grid &g, int H, int zw) { re
 // in, the words at x + c_i out.  A pair with a wall face next to either cell
 // takes the per-node path.
 template <class C, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_read_min_blocks<C, true>())) k_aa_odd_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_four_min_blocks<C>())) k_aa_odd_zp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
@@ -668,13 +668,9 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, PairWord<C>::kMinBlocks) k_ts_s
   }
 }
 
-// One-step push (PUSH) or pull in z pairs.  The push reads its own word, so
-// on a z-periodic box the next pair plane's words are loaded before this
-// plane's collision (FP16 push 74.3 -> 76.2 GFLUP/s on 256^3 with four
-// planes per thread).  The pull and the AA odd step read neighbour words;
-// the same prefetch there measured 3 % slower (AA odd, FP16).
+// One-step push (PUSH) or pull in z pairs.
 template <class C, bool PUSH, bool FORCE, bool RED>
-__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_read_min_blocks<C, !PUSH>())) k_os_zp(StepParams p) {
+__global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_four_min_blocks<C>())) k_os_zp(StepParams p) {
   chain_wait();
   using PW = PairWord<C>;
   using W = typename PW::W;
@@ -688,98 +684,56 @@ __global__ void __launch_bounds__(LBM_STEP_MAXT, (pair_read_min_blocks<C, !PUSH>
     const int64_t nw = p.npad >> 1;
     const bool col = zp_open_column(g, x, y);
     const bool inner = zp_inner_warp(g, x, y);
-    // push on a z-periodic box, open column: the next pair plane's words
-    // (node-local reads of A) are loaded before this plane's collision
-    if (PUSH && col && g.pz) {
-      auto push = [&](auto tag, int zw, W(&v)[Q]) {
+    for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
+      auto pair = [&](auto tag) {
         constexpr bool INNER = decltype(tag)::value;
-        const int xs = launder(x), ys = launder(y);
-        const int ws = xs + (int)g.sx * ys + (int)g.sxy * zw;
-        ZPairCol c;
-        if (!INNER) c.set(g, xs, ys);
-        B[ws] = v[0];
+        const int w = x + (int)g.sx * y + (int)g.sxy * zw;
+        W v[Q];
+        if (PUSH) {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          bool seam;
-          const int d = c.template nbw<1, INNER>(g, H, ws, zw, i, seam);
-          B[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
-        }
-      };
-      const int step = (int)g.sxy * (int)gridDim.z;
-      int zw = blockIdx.z;
-      int w = x + (int)g.sx * y + (int)g.sxy * zw;
-      W v[Q];
-      if (zw < H) {
+          for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
+        } else {
+          ZPairCol c;
+          if (!INNER) c.set(g, x, y);
+          v[0] = A[w];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
-      }
-      for (; zw < H; zw += gridDim.z) {
-        W n[Q];
-        if (zw + (int)gridDim.z < H) {
-#pragma unroll
-          for (int i = 0; i < Q; ++i) n[i] = A[i * nw + w + step];
+          for (int i = 1; i < Q; ++i) {
+            bool seam;
+            const W t = A[i * nw + c.template nbw<-1, INNER>(g, H, w, zw, i, seam)];
+            v[i] = seam ? PW::swap(t) : t;
+          }
         }
         zp_collide_pair<C, FORCE>(v, p, m, j);
-        if (inner && zp_inner_plane(H, zw))
-          push(InnerTag{}, launder(zw), v);
-        else
-          push(FaceTag{}, launder(zw), v);
-        w += step;
+        // recompute the addresses rather than hold them across the collision
+        const int ws = launder(w), xs = launder(x), ys = launder(y);
+        if (PUSH) {
+          ZPairCol c;
+          if (!INNER) c.set(g, xs, ys);
+          B[ws] = v[0];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = n[i];
-      }
-    } else {
-      for (int zw = blockIdx.z; zw < H; zw += gridDim.z) {
-        auto pair = [&](auto tag) {
-          constexpr bool INNER = decltype(tag)::value;
-          const int w = x + (int)g.sx * y + (int)g.sxy * zw;
-          W v[Q];
-          if (PUSH) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) v[i] = A[i * nw + w];
-          } else {
-            ZPairCol c;
-            if (!INNER) c.set(g, x, y);
-            v[0] = A[w];
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-              bool seam;
-              const W t = A[i * nw + c.template nbw<-1, INNER>(g, H, w, zw, i, seam)];
-              v[i] = seam ? PW::swap(t) : t;
-            }
+          for (int i = 1; i < Q; ++i) {
+            bool seam;
+            const int d = c.template nbw<1, INNER>(g, H, ws, zw, i, seam);
+            B[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
           }
-          zp_collide_pair<C, FORCE>(v, p, m, j);
-          // recompute the addresses rather than hold them across the collision
-          const int ws = launder(w), xs = launder(x), ys = launder(y);
-          if (PUSH) {
-            ZPairCol c;
-            if (!INNER) c.set(g, xs, ys);
-            B[ws] = v[0];
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-              bool seam;
-              const int d = c.template nbw<1, INNER>(g, H, ws, zw, i, seam);
-              B[i * nw + d] = seam ? PW::swap(v[i]) : v[i];
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) B[i * nw + ws] = v[i];
-          }
-        };
-        if (inner && zp_inner_plane(H, zw)) {
-          pair(InnerTag{});
-        } else if (col && zp_open_plane(g, H, zw)) {
-          pair(FaceTag{});
         } else {
-          const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
-          for (int h = 0; h < 2; ++h) {
-            ZPairNode a;
-            a.set(g, x, y, zw + h * H);
-            if (PUSH)
-              os_push_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
-            else
-              os_pull_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
-          }
+#pragma unroll
+          for (int i = 0; i < Q; ++i) B[i * nw + ws] = v[i];
+        }
+      };
+      if (inner && zp_inner_plane(H, zw)) {
+        pair(InnerTag{});
+      } else if (col && zp_open_plane(g, H, zw)) {
+        pair(FaceTag{});
+      } else {
+        const Lattice<C, 0> LA = lattice_of<C, 0>(p.A, p), LB = lattice_of<C, 0>(p.B, p);
+        for (int h = 0; h < 2; ++h) {
+          ZPairNode a;
+          a.set(g, x, y, zw + h * H);
+          if (PUSH)
+            os_push_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
+          else
+            os_pull_node<false, C, 0, ZPairNode, FORCE>(p, a, LA, LB, m, j);
         }
       }
     }
